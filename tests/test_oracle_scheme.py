@@ -1,0 +1,271 @@
+"""Scheme-level pins of the oracle: the paper's printed accuracy tables (Sec. 3.1,
+Tables 1-2; Sec. 3.3, Table 4), convergence orders, free-stream preservation,
+conservation on periodic domains, mirror symmetry, the exact Riemann solution
+for the Sod tube, hybrid == linear when nothing is flagged, robustness on the
+blast wave, and the boundary and time-step rules."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import exact_riemann as ER
+import oracle
+from paper_2304_05572_gb300 import problems as P
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            rows[int(parts[0].split("/")[1])] = np.array([float(v) for v in parts[1:4]])
+    return rows
+
+
+def _norms(e):
+    e = np.asarray(e).ravel()
+    return np.array([np.mean(np.abs(e)), math.sqrt(np.mean(e * e)), np.max(np.abs(e))])
+
+
+def _sine1d(inv_h, mode):
+    n = 2 * inv_h
+    cfg, W, t_end = P.sine_1d(n, recon_mode=mode)
+    W2, t, steps, _ = oracle.run(cfg, W, t_end, threads=1)
+    return _norms(W2[0, 0] - P.sine_1d_exact(n, t)), W2
+
+
+# tolerances on the relative mismatch with the printed tables, per mesh (coarse meshes
+# amplify the unpublished choices: gamma_Hi, gamma_Lo, error-norm conventions)
+TOL1 = {5: 0.03, 10: 0.02, 20: 0.005, 40: 0.0015, 80: 0.0025}
+
+
+@pytest.mark.parametrize("inv_h", [5, 10, 20, 40, 80])
+def test_sine1d_reproduces_table1_wenoao(inv_h):
+    ref = _golden("table1_sine1d_wenoao.txt")[inv_h]
+    err, _ = _sine1d(inv_h, "wenoao")
+    np.testing.assert_array_less(np.abs(err / ref - 1.0), TOL1[inv_h])
+
+
+@pytest.mark.parametrize("inv_h", [5, 10, 20, 40, 80])
+def test_sine1d_hybrid_matches_table2(inv_h):
+    """Soft pin: no cell of the smooth sine is troubled (Steps 1-3), so the hybrid run is the
+    linear-upwind run; Table 2 lies within 2.5% of it on every mesh."""
+    ref = _golden("table2_sine1d_hybrid.txt")[inv_h]
+    err, _ = _sine1d(inv_h, "hybrid")
+    np.testing.assert_array_less(np.abs(err / ref - 1.0), 0.03)
+
+
+@pytest.mark.parametrize("inv_h", [10, 20])
+def test_sine1d_wenoao_over_linear_ratio_matches_tables(inv_h):
+    """The smooth sine flags no cell, so Table 2 is the linear-upwind run and the
+    Table 1 / Table 2 ratio isolates what the nonlinear weights of Eq. (37) do.  With
+    delta/(beta_k + eps) squared and gamma_Hi = gamma_Lo = 0.85 the oracle's
+    WENO-AO / linear ratio matches the printed one (L1 and Linf to 1% of its deviation from 1)."""
+    t1 = _golden("table1_sine1d_wenoao.txt")[inv_h]
+    t2 = _golden("table2_sine1d_hybrid.txt")[inv_h]
+    e_ao, _ = _sine1d(inv_h, "wenoao")
+    e_lin, _ = _sine1d(inv_h, "linear")
+    paper = t1 / t2 - 1.0
+    ours = e_ao / e_lin - 1.0
+    np.testing.assert_allclose(ours[[0, 2]], paper[[0, 2]], rtol=0.01)   # L1, Linf
+    np.testing.assert_allclose(ours[1], paper[1], rtol=0.05)             # L2 (definition unprinted)
+
+
+def test_sine1d_fifth_order_and_hybrid_equals_linear():
+    errs = []
+    for inv_h in (10, 20, 40):
+        e_h, W_h = _sine1d(inv_h, "hybrid")
+        e_l, W_l = _sine1d(inv_h, "linear")
+        assert np.array_equal(W_h, W_l)          # nothing flagged -> identical bits
+        errs.append(e_h)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 4.85
+
+
+def test_sine1d_no_flags_and_wenoao_all_flags():
+    cfg, W, _ = P.sine_1d(20)
+    _, _, fl = oracle.step_flags(cfg, W)
+    assert fl[(0, 0, "normal")].sum() == 0 and fl[(1, 0, "normal")].sum() == 0
+    cfg["recon_mode"] = "wenoao"
+    _, _, fl = oracle.step_flags(cfg, W)
+    assert fl[(0, 0, "normal")].all() and fl[(1, 0, "normal")].all()
+
+
+@pytest.mark.parametrize("inv_h", [5, 10])
+def test_sine2d_wenoao_matches_table4(inv_h):
+    """Sec. 3.3 reads no end time; with t = 2 (as in Sec. 3.1) the errors lie within 5% of Table 4."""
+    n = 2 * inv_h
+    cfg, W, t_end = P.sine_2d(n, recon_mode="wenoao")
+    W2, t, _, _ = oracle.run(cfg, W, t_end)
+    err = _norms(W2[0] - P.sine_2d_exact(n, t))
+    ref = _golden("table4_sine2d_wenoao.txt")[inv_h]
+    np.testing.assert_array_less(np.abs(err / ref - 1.0), 0.05)
+
+
+def test_sine2d_fifth_order():
+    errs = []
+    for n in (10, 20):
+        cfg, W, t_end = P.sine_2d(n)
+        W2, t, _, _ = oracle.run(cfg, W, t_end)
+        errs.append(_norms(W2[0] - P.sine_2d_exact(n, t)))
+    assert np.log2(errs[0] / errs[1]).min() > 4.8
+
+
+@pytest.mark.parametrize("bc", ["periodic", "extrap", "reflect", "noslip"])
+def test_free_stream_preserved_bitwise(bc):
+    state = (1.3, 0.4, -0.7, 2.1) if bc in ("periodic", "extrap") else (1.3, 0.0, 0.0, 2.1)
+    cfg, W, _ = P.uniform_2d(12, state=state, bc=bc, ny=9)
+    W2, _, steps, _ = oracle.run(cfg, W, 10.0, max_steps=3)
+    assert steps == 3
+    assert np.array_equal(W2, W)
+
+
+def test_free_stream_preserved_1d():
+    cfg, W, _ = P.sod_1d(40)
+    W[:] = W[:, :, :1]
+    W2, _, _, _ = oracle.run(cfg, W, 10.0, max_steps=3)
+    assert np.array_equal(W2, W)
+
+
+def test_conservation_periodic_2d():
+    cfg, W, _ = P.riemann4_2d(24)
+    cfg["bc"] = ["periodic"] * 4
+    s0 = W.sum(axis=(1, 2))
+    W2, _, steps, _ = oracle.run(cfg, W, 10.0, max_steps=4)
+    s1 = W2.sum(axis=(1, 2))
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * np.abs(W).sum() * steps)
+
+
+def test_conservation_periodic_1d():
+    cfg, W, _ = P.sod_1d(64)
+    cfg["bc"] = ["periodic"] * 4
+    s0 = W.sum(axis=(1, 2))
+    W2, _, steps, _ = oracle.run(cfg, W, 10.0, max_steps=10)
+    assert np.all(np.abs(W2.sum(axis=(1, 2)) - s0) <= 1e-13 * np.abs(W).sum() * steps)
+
+
+def test_sod_mirror_symmetry():
+    cfg, W, t_end = P.sod_1d(100)
+    Wm = W[:, :, ::-1].copy()
+    Wm[1] = -Wm[1]
+    A, _, _, _ = oracle.run(cfg, W, t_end)
+    B, _, _, _ = oracle.run(cfg, Wm, t_end)
+    Bm = B[:, :, ::-1].copy()
+    Bm[1] = -Bm[1]
+    assert np.max(np.abs(A - Bm)) <= 1e-12 * np.max(np.abs(A))
+
+
+def test_riemann2d_diagonal_symmetry():
+    """Quadrant data symmetric under x <-> y with u <-> v stays symmetric."""
+    st = [(1.0, 0.2, 0.2, 1.0), (0.5, 0.1, -0.3, 0.6), (0.8, -0.4, -0.4, 0.9), (0.5, -0.3, 0.1, 0.6)]
+    cfg = P.base_config(2, 20, 20, 0, 1, 0, 1, bc=["extrap"] * 4)
+    W = P._quadrants(20, 20, st)
+    np.testing.assert_allclose(W[0], W[0].T, atol=1e-15)
+    W2, _, _, _ = oracle.run(cfg, W, 1.0, max_steps=5)
+    np.testing.assert_allclose(W2[0], W2[0].T, atol=1e-13)
+    np.testing.assert_allclose(W2[1], W2[2].T, atol=1e-13)
+    np.testing.assert_allclose(W2[3], W2[3].T, atol=1e-13)
+
+
+def test_sod_against_exact_riemann_solution():
+    errs = []
+    for n in (100, 200):
+        cfg, W, t_end = P.sod_1d(n)
+        W2, t, _, _ = oracle.run(cfg, W, t_end)
+        ex = ER.cell_averages((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.5, t, np.linspace(0, 1, n + 1))
+        errs.append(np.mean(np.abs(W2[0, 0] - ex[0])))
+    assert errs[1] < 2.5e-3
+    assert errs[0] / errs[1] > 1.5            # first-order convergence at the discontinuities
+
+
+def test_sod_hybrid_flags_only_near_waves():
+    cfg, W, t_end = P.sod_1d(200)
+    W2, _, _, _ = oracle.run(cfg, W, t_end)
+    _, _, fl = oracle.step_flags(cfg, W2)
+    f = fl[(0, 0, "normal")][0, 1:-1].astype(bool)
+    assert 0.02 < f.mean() < 0.3
+    assert not f[:40].any()       # undisturbed left state (x < 0.2)
+
+
+def test_blast_wave_robust():
+    cfg, W, t_end = P.blast_1d(200)
+    W2, t, steps, _ = oracle.run(cfg, W, t_end)
+    assert abs(t - t_end) < 1e-12
+    assert np.all(W2[0] > 0)
+
+
+def test_spreading_step4():
+    """A single raw-troubled cell flags itself and both neighbours (Step 4)."""
+    n = 40
+    cfg = P.base_config(1, n, 1, 0.0, 1.0, bc=["extrap"] * 4)
+    rho = np.ones(n)
+    rho[20:] = 0.5
+    W = P.conservative(rho, np.zeros(n), 0 * rho, np.ones(n), dim=1)[:, None, :]
+    _, _, fl = oracle.step_flags(cfg, np.ascontiguousarray(W))
+    f = fl[(0, 0, "normal")][0]          # cells -1..n
+    Z1 = oracle.zeta1_scaled("B", 1.0 / n)
+    raw = []
+    for i in range(-2, n + 2):
+        q = [rho[min(max(k, 0), n - 1)] for k in range(i - 2, i + 3)]
+        raw.append(oracle.indicator(np.array(q), Z1))
+    raw = np.array(raw)
+    expect = raw[:-2] | raw[1:-1] | raw[2:]
+    assert np.array_equal(f, expect.astype(np.uint8))
+    assert f.sum() >= 3
+
+
+def test_ghost_fill_rules():
+    cfg, W, _ = P.random_smooth_2d(6, 5)
+    NG = oracle.NG
+    cfg["bc"] = ["periodic", "extrap", "reflect", "noslip"]
+    Wp = oracle.fill_ghosts(cfg, W)
+    nx, ny = 6, 5
+    I = lambda i: i + NG
+    J = lambda j: j + NG
+    for l in range(1, NG + 1):
+        np.testing.assert_array_equal(Wp[:, J(0):J(ny), I(-l)], W[:, :, nx - l])            # periodic x-lo
+        np.testing.assert_array_equal(Wp[:, J(0):J(ny), I(nx - 1 + l)], W[:, :, nx - 1])    # extrap x-hi
+        m = W[:, l - 1, :].copy(); m[2] = -m[2]                                              # reflect y-lo
+        np.testing.assert_array_equal(Wp[:, J(-l), I(0):I(nx)], m)
+        m = W[:, ny - l, :].copy(); m[1] = -m[1]; m[2] = -m[2]                               # no-slip y-hi
+        np.testing.assert_array_equal(Wp[:, J(ny - 1 + l), I(0):I(nx)], m)
+
+
+def test_cfl_time_step_rule():
+    cfg, W, _ = P.riemann4_2d(16)
+    r = W[0]; u = W[1] / r; v = W[2] / r
+    p = 0.4 * (W[3] - 0.5 * r * (u * u + v * v))
+    a = np.sqrt(1.4 * p / r)
+    h = 1.0 / 16
+    assert oracle.cfl_dt(cfg, W) == pytest.approx(0.5 * np.min(h / (np.sqrt(u * u + v * v) + a)), rel=1e-14)
+    cfg2, W2, _ = P.viscous_shock_tube(16, 8, Re=50.0)
+    r = W2[0]; u = W2[1] / r; v = W2[2] / r
+    p = 0.4 * (W2[3] - 0.5 * r * (u * u + v * v))
+    a = np.sqrt(1.4 * p / r)
+    h = 1.0 / 16
+    nu = (1 / 50.0) / r
+    expect = 0.3 * np.min(np.minimum(h / (np.sqrt(u * u + v * v) + a), h * h / (4 * nu)))
+    assert oracle.cfl_dt(cfg2, W2) == pytest.approx(expect, rel=1e-14)
+
+
+def test_viscous_shock_tube_runs():
+    cfg, W, _ = P.viscous_shock_tube(40, 20, Re=200.0)
+    W2, t, steps, _ = oracle.run(cfg, W, 1.0, max_steps=5)
+    assert steps == 5 and np.all(np.isfinite(W2)) and np.all(W2[0] > 0)
+    # a no-slip mirror (both velocities negated, y kept) is not a symmetry of the BGK
+    # equation once tangential gradients exist, so the wall mass flux is only nearly zero
+    assert abs(W2[0].sum() - W[0].sum()) <= 1e-5 * W[0].sum()
+    cfg["bc"] = ["reflect"] * 4           # slip walls: exact mirror symmetry -> no wall flux
+    W3, _, _, _ = oracle.run(cfg, W, 1.0, max_steps=5)
+    assert abs(W3[0].sum() - W[0].sum()) <= 1e-13 * W[0].sum()
+
+
+def test_t_end_is_hit_exactly():
+    cfg, W, _ = P.sod_1d(50)
+    W2, t, steps, last = oracle.run(cfg, W, 0.0123)
+    assert t == pytest.approx(0.0123, abs=1e-15) and last > 0
