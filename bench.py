@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the hybrid WENO-AO gas-kinetic S2O4 step on GB300.
+
+Workload: the four-quadrant 2D Riemann problem on [0,1]^2 at 1024^2 cells with
+seeded quadrant states (rho, p ~ U[0.1, 2], u, v ~ U[-1, 1], numpy PCG64 seed
+20230411), hybrid WENO-AO reconstruction, c1 = 0.01, c2 = 1, CFL 0.5,
+non-reflecting boundaries, FP64.  One "step" is one S2O4 step (two stages) over
+the whole grid; the unit is interior cells x stages.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched under torchrun) every rank advances its own
+independent replica (the solves do not exchange data) and the value is the
+aggregate over ranks divided by the maximum time over ranks.
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+paper's method) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mcell-stage updates/s, 2D GKS FP64, served vs plain launch; p50/p99 solve latency"
+UNIT = "Mcell-stage/s"
+N_SIDE = 1024
+WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS, S2O4"
+
+# FP64 operations executed per Gauss-point flux evaluation of the 2D kernel with tau > 0
+# (DADD + DMUL + 2 x DFMA instructions per thread, ncu, 256^2 four-quadrant Riemann step).
+FLUX_FLOP_PER_GP_2D = None
+# Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1])); smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def cpu_oracle_rate(n_side, steps, threads=0):
+    """Time the oracle (as it stands) on `steps` S2O4 steps of the n_side^2 workload."""
+    import oracle
+    from paper_2304_05572_gb300 import problems as P
+    oracle.build()
+    cfg, W, _ = P.riemann4_2d(n_side)
+    t0 = time.perf_counter()
+    _, _, n, _ = oracle.run(cfg, W, 1e9, max_steps=steps, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_side * n_side * 2 * n / dt / 1e6, dt, oracle.threads_used(threads)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    n_side = 256
+    cores = None
+    for _ in range(args.warmup):
+        cpu_oracle_rate(n_side, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, cores = cpu_oracle_rate(n_side, 1)
+    dt = time.perf_counter() - t0
+    value = n_side * n_side * 2 * args.steps / dt / 1e6
+    sample = "%d S2O4 steps of the same problem at %d^2 cells (1/16 of the 1024^2 grid; per-cell work unchanged)" % (
+        args.steps, n_side)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_SIDE, N_SIDE], "stages_per_step": 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+
+    if args.impl == "reference":
+        if dist is not None:
+            dist.init_process_group("gloo")
+        rc = run_reference(args, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    from paper_2304_05572_gb300 import hgks, problems as P
+
+    torch.cuda.set_device(local_rank)
+    if dist is not None:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+
+    n = args.n
+    cfg, W0, _ = P.riemann4_2d(n)
+    cells = n * n
+    solver = hgks.Solver(cfg, stream=stream)
+    W0 = np.ascontiguousarray(W0)
+    Wd = torch.from_numpy(W0).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident timing: W steps untimed, then K timed steps (L2 flushed before each)
+    solver.hgks_set_state(Wd)
+    for _ in range(args.warmup):
+        solver.hgks_step(1e9, 1, wait=False)
+    torch.cuda.synchronize()
+    solver.hgks_set_timing(True)
+    solver.hgks_get_timing()              # drop warm-up records (timing starts now)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0) as clk:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                solver.hgks_step(1e9, 1, wait=False)
+                ev[k][1].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    timing = solver.hgks_get_timing()
+    solver.hgks_set_timing(False)
+    stats = solver.hgks_get_stats()
+    if stats["status"] != 0:
+        raise SystemExit("solver reported status %d" % stats["status"])
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_timed = args.steps
+    value = world * cells * 2 * steps_timed / (ms * 1e-3) / 1e6
+    troubled = stats["troubled"].sum() / max(1, stats["examined"].sum())
+
+    # ---- end-to-end through the C ABI: pinned host state in, one step, pinned host state out
+    Wh = torch.from_numpy(W0).pin_memory()
+    Wout = torch.empty_like(Wh).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.hgks_set_state(Wh)                # H2D from pinned host memory (waits for the copy)
+        solver.hgks_step(1e9, 1, wait=False)
+        solver.hgks_get_state(Wout)              # D2H of the result (waits for the stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * cells * 2 * e2e_steps / e2e_s / 1e6
+    state_bytes = int(W0.nbytes)
+
+    # ---- dominant kernel roofline (FP64 ALU)
+    flux_ms, flux_calls = timing.get("gks_flux", (0.0, 0))
+    launches = int(stats.get("launches", 0))
+    roofline = None
+    if flux_calls:
+        avg_ms = flux_ms / flux_calls
+        gp_per_launch = 2 * (n + 1) * n          # Gauss points of one sweep
+        if FLUX_FLOP_PER_GP_2D:
+            achieved = FLUX_FLOP_PER_GP_2D * gp_per_launch / (avg_ms * 1e-3) / 1e12
+            roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                        "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                        "kernel": "gks_flux", "avg_launch_ms": avg_ms,
+                        "peak_note": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (1.25 TFLOP/s nominal)"}
+        else:
+            roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                        "frac": None, "traffic": None, "kernel": "gks_flux", "avg_launch_ms": avg_ms}
+    shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in timing.values())), 4) for k, v in timing.items() if v[1]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_timed,
+        "warmup": args.warmup, "ms_per_step": ms / steps_timed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_SIDE else WORKLOAD.replace("1024^2", "%d^2" % n),
+                   "grid": [n, n], "stages_per_step": 2, "replicas": world,
+                   "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                   "troubled_fraction": round(float(troubled), 5)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "note": "hgks_set_state(pinned host) + hgks_step(1) + hgks_get_state(pinned host) per step"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernel_time_share": shares,
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, secs, cores = cpu_oracle_rate(N_SIDE, 1)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "1 S2O4 step of the same 1024^2 problem (%.1f s)" % secs}
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.hgks_destroy_solver()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * hgks.h -- C ABI of the GB300 (sm_103a) FP64 hybrid WENO-AO gas-kinetic solver.
+ *
+ * The library advances the finite-volume semi-discretisation W_t = L(W) of the
+ * 1D / 2D Euler or Navier-Stokes equations (arXiv 2304.05572, Sec. 2, Eq. (1))
+ * on a uniform structured grid with the two-stage fourth-order (S2O4) time
+ * integrator of Sec. 2.2.  Each stage evaluates, for every interface, the
+ * extreme-point troubled-cell indicator (Sec. 2.3.1, Steps 1-4), linear-upwind
+ * or characteristic WENO-AO reconstruction of the values and normal and
+ * tangential derivatives at the interface Gauss points (Sec. 2.3.1 Step 5,
+ * Eqs. (26)-(45); Sec. 2.3.3), the kinetic weighting of the equilibrium
+ * (Eqs. (46)-(47)) and the time-integrated second-order gas-kinetic flux
+ * (Sec. 2.1, Eqs. (6)-(12)).  All arithmetic is IEEE FP64 on the GPU.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (HGKS_OK) or a negative HGKS_E* code; no exception crosses the ABI.
+ *   - The state is the conservative cell averages W, laid out [nv][ny][nx] in C
+ *     order (nv = 3 in 1D: rho, rho U, rho E; nv = 4 in 2D: rho, rho U, rho V, rho E),
+ *     FP64.  Caller-provided buffers stay owned by the caller; the library never
+ *     keeps a pointer to them after the call returns.
+ *   - A solver owns its device memory and works on the CUDA stream given at
+ *     creation (NULL = the legacy default stream).  A solver is not thread-safe;
+ *     distinct solvers on distinct streams may be used from distinct threads.
+ *   - hgks_last_error(s) returns a static, human-readable description of the
+ *     last failure on s (or of the last create failure when s is NULL).
+ */
+#ifndef HGKS_H
+#define HGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HGKS_OK 0
+#define HGKS_EINVAL (-1)         /* invalid argument or configuration */
+#define HGKS_ENOMEM (-2)         /* device or host allocation failed */
+#define HGKS_ENONPHYSICAL (-3)   /* rho <= 0, p <= 0 or non-finite state detected on the device */
+#define HGKS_ETIMEOUT (-4)       /* a bounded device wait ran out */
+#define HGKS_ECUDA (-5)          /* a CUDA runtime call failed */
+
+/* boundary conditions (Sec. 3: periodic, non-reflecting, reflecting, symmetric, no-slip adiabatic) */
+enum { HGKS_BC_PERIODIC = 0, HGKS_BC_EXTRAP = 1, HGKS_BC_REFLECT = 2, HGKS_BC_SYMMETRY = 3, HGKS_BC_NOSLIP = 4 };
+/* reconstruction: hybrid (the paper's method), linear upwind only, WENO-AO everywhere (Sec. 3, Tables 1 and 4) */
+enum { HGKS_RECON_HYBRID = 0, HGKS_RECON_LINEAR = 1, HGKS_RECON_WENOAO = 2 };
+/* readings of zeta1 = "5/17 dx" in Step 1 (Sec. 2.3.1): A = (5/17) dx, B = 5/(17 dx) (default), C = 5/17 in cell units */
+enum { HGKS_ZETA1_A = 0, HGKS_ZETA1_B = 1, HGKS_ZETA1_C = 2 };
+
+typedef struct hgks_config {
+    int dim;                  /* 1 or 2 */
+    int nx, ny;               /* interior cells; ny = 1 in 1D */
+    double x0, x1, y0, y1;    /* domain [x0,x1] x [y0,y1] */
+    double gamma;             /* ratio of specific heats (Sec. 3: 1.4) */
+    int viscous;              /* 0: Euler, tau = c1 dt + c2 |pl-pr|/(pl+pr) dt; 1: Navier-Stokes, tau = mu/p + c2 ... (Sec. 3) */
+    double mu, prandtl;       /* dynamic viscosity (1/Re); Prandtl number (only Pr = 1, the BGK value, is accepted) */
+    double c1, c2;            /* collision-time constants (Sec. 3) */
+    double cfl;               /* dt = cfl min(h/(|U|+a), h^2/(4 nu)), h = min(dx, dy), nu = mu/rho */
+    double fixed_dt;          /* > 0: use this dt instead of the CFL rule (Sec. 3.1 uses dt = 0.2 dx) */
+    int tau_zero;             /* 1: tau = 0 (Sec. 3.1, 3.3) */
+    int bc[4];                /* x-lo, x-hi, y-lo, y-hi: HGKS_BC_* */
+    int recon_mode;           /* HGKS_RECON_* */
+    int zeta1_mode;           /* HGKS_ZETA1_* */
+    double gamma_hi, gamma_lo;/* WENO-AO linear weights, Eq. (35) (0.85, 0.85) */
+    double eps;               /* WENO-AO epsilon, Eq. (37) (1e-8) */
+} hgks_config;
+
+typedef struct hgks_stats {
+    long long steps;          /* S2O4 steps taken since set_state */
+    double t;                 /* simulation time */
+    double last_dt;           /* dt of the last step */
+    int status;               /* 0 or the HGKS_E* code latched on the device */
+    int pad_;
+    /* troubled counts accumulated over all steps: [stage][sweep x/y][0 = normal cells, 1 = tangential passes] */
+    long long troubled[2][2][2];
+    /* number of candidates counted by troubled[][][] (cells resp. passes examined) */
+    long long examined[2][2][2];
+    /* kernels this solver enqueued since the last hgks_set_state (host-side count) */
+    long long launches;
+} hgks_stats;
+
+typedef struct hgks_solver hgks_solver;
+
+/* Fill *cfg with the paper's defaults (gamma 1.4, c1 0.01, c2 1, CFL 0.5, hybrid, reading B,
+ * gamma_hi = gamma_lo = 0.85, eps 1e-8, periodic boundaries).  Returns HGKS_EINVAL on NULL. */
+int hgks_config_default(hgks_config* cfg);
+
+/* Validate *cfg and allocate the solver and its device buffers on the current
+ * CUDA device.  stream: a cudaStream_t cast to void* (NULL = default stream).
+ * On success *out owns the solver; free it with hgks_destroy_solver.
+ * Errors: HGKS_EINVAL (bad config, see hgks_last_error(NULL)), HGKS_ENOMEM, HGKS_ECUDA. */
+int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_solver** out);
+
+/* Release every resource of s (NULL is a no-op).  Synchronises s's stream first. */
+void hgks_destroy_solver(hgks_solver* s);
+
+/* Copy the conservative cell averages W ([nv][ny][nx], FP64) into the solver,
+ * reset time to t0 and the step and troubled counters to zero and clear the
+ * latched status.  on_device = 0: W is host memory (pageable or pinned);
+ * 1: W is device memory of the solver's device.  The copy is ordered on the
+ * solver's stream; the call returns after W may be reused by the caller. */
+int hgks_set_state(hgks_solver* s, const double* W, int on_device, double t0);
+
+/* Advance by whole S2O4 steps until the time reaches t_end (the last step is
+ * shortened to land on it; the run stops once t_end - t <= 1e-12 max(1, |t_end|))
+ * or max_steps steps were taken.  All work is enqueued on the solver's stream;
+ * dt is computed and clipped on the device.  If steps_done is non-NULL the call
+ * waits for the stream and stores the number of steps actually taken; with
+ * steps_done == NULL it returns after enqueueing (errors latched on the device
+ * surface at the next waiting call).  Returns HGKS_ENONPHYSICAL if a
+ * non-physical state was detected (the solver then stops advancing). */
+int hgks_step(hgks_solver* s, double t_end, int max_steps, int* steps_done);
+
+/* Copy the state out ([nv][ny][nx], FP64) to host (on_device = 0) or device (1)
+ * memory.  Waits for the solver's stream. */
+int hgks_get_state(hgks_solver* s, double* W, int on_device);
+
+/* Current simulation time (waits for the stream). */
+int hgks_get_time(hgks_solver* s, double* t);
+
+/* Step count, last dt, latched status and troubled-cell counters (waits for the stream). */
+int hgks_get_stats(hgks_solver* s, hgks_stats* st);
+
+/* Troubled flags of the last step (parity hook).  stage 0/1, sweep 0 (x) / 1 (y),
+ * kind 0: final (Step-4 spread) flag of every cell the normal reconstruction of
+ * the sweep visits, laid out [nt+6][nn+2] (2D) or [1][nn+2] (1D), entry
+ * [t+3][n+1] for line t in [-3, nt+2] and cell n in [-1, nn];
+ * kind 1 (2D only): bits 0..3 = final flags of the tangential passes of
+ * Q^l, Q^r, Q^l_n, Q^r_n at interface m of line t, laid out [nt][nn+1].
+ * nn / nt = cell counts normal / tangential to the sweep (x: nn = nx, nt = ny).
+ * Flags are recorded only when hgks_set_flag_capture(s, 1) is active.
+ * out must hold the stated number of bytes (see hgks_flags_size). */
+int hgks_set_flag_capture(hgks_solver* s, int enable);
+size_t hgks_flags_size(const hgks_solver* s, int sweep, int kind);
+int hgks_get_flags(hgks_solver* s, int stage, int sweep, int kind, uint8_t* out);
+
+/* Per-kernel-class timing (CUDA events on the solver's stream), for profiling.
+ * enable = 1 records an event pair around every launch of every class; the
+ * totals are summed until reset.  names: kernel class names, ms: total ms,
+ * calls: launches; returns the number of classes written (<= cap). */
+int hgks_set_timing(hgks_solver* s, int enable);
+int hgks_get_timing(hgks_solver* s, int cap, const char** names, double* ms, long long* calls);
+
+/* Description of the last error on s (or of the last create/validation error if s is NULL). */
+const char* hgks_last_error(const hgks_solver* s);
+
+/* Number of device bytes a solver of this configuration allocates (for admission control). */
+size_t hgks_footprint_bytes(const hgks_config* cfg);
+
+/* ------------------------------------------------------------------------ */
+/* Batched execution: many independent solvers advanced together.            */
+/* ------------------------------------------------------------------------ */
+
+/* Advance every solver in solvers[0..n-1] by one S2O4 step each (each with its
+ * own dt and its own t_end), enqueued on the given stream as one set of
+ * multi-solve launches per stage (one launch per kernel class, whose blocks are
+ * distributed over all solvers' tiles), instead of one launch set per solver.
+ * Results are identical to stepping each solver alone.  All solvers must live
+ * on the current device; their own streams are ordered before and after the
+ * batch by events.  t_end[i] as in hgks_step; a solver already at its t_end or
+ * with a latched error is left unchanged.  stream: cudaStream_t cast to void*. */
+int hgks_batch_step(hgks_solver* const* solvers, int n, const double* t_end, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGKS_H */

@@ -1,1 +1,15 @@
-"""GB300-native (sm_103a) FP64 hot path of the hybrid WENO-AO gas-kinetic scheme."""
+"""GB300-native (sm_103a) FP64 hot path of the high-order gas-kinetic scheme with
+hybrid WENO-AO reconstruction (arXiv 2304.05572).
+
+The computation runs in the CUDA library behind the C ABI of ``include/hgks.h``;
+``hgks`` is its Python binding (ctypes, argument marshalling only) and
+``problems`` holds the seeded initial data of the test problems.
+"""
+from . import problems  # noqa: F401
+
+__all__ = ["problems", "hgks", "build"]
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)

@@ -1,0 +1,466 @@
+// hgks_api.cu -- the C ABI of the solver (declared in include/hgks.h): configuration
+// checks, the device memory pool of a solver, state transfer, the step loop, parity
+// hooks (flags), per-kernel timing and batched stepping.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hgks.h"
+#include "hgks_internal.h"
+
+using namespace hgks;
+
+namespace {
+
+thread_local char g_create_err[512] = "";
+
+void set_err(char* buf, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+double zeta1_scaled(int mode, double h)
+{
+    // Z1 = 17 zeta1 h^2 for the Step-1 test |D| <= Z1 (Sec. 2.3.1, Eq. (24))
+    if (mode == HGKS_ZETA1_A) return 5.0 * h * h * h;
+    if (mode == HGKS_ZETA1_C) return 5.0;
+    return 5.0 * h;
+}
+
+double dof_K(int dim, double gam)
+{
+    // Sec. 2.1: K = (5 - 3 gamma)/(gamma - 1) + 1 in 2D; 1D: (3 - gamma)/(gamma - 1)
+    if (dim == 2) return (5.0 - 3.0 * gam) / (gam - 1.0) + 1.0;
+    return (3.0 - gam) / (gam - 1.0);
+}
+
+int validate(const hgks_config* c, char* err)
+{
+    if (!c) { set_err(err, "config is NULL"); return HGKS_EINVAL; }
+    if (c->dim != 1 && c->dim != 2) { set_err(err, "dim must be 1 or 2 (got %d)", c->dim); return HGKS_EINVAL; }
+    if (c->nx < NG) { set_err(err, "nx must be >= %d (got %d)", NG, c->nx); return HGKS_EINVAL; }
+    if (c->dim == 1 && c->ny != 1) { set_err(err, "ny must be 1 in 1D"); return HGKS_EINVAL; }
+    if (c->dim == 2 && c->ny < NG) { set_err(err, "ny must be >= %d (got %d)", NG, c->ny); return HGKS_EINVAL; }
+    if ((long long)c->nx * c->ny > (1LL << 28)) { set_err(err, "grid too large (%d x %d)", c->nx, c->ny); return HGKS_EINVAL; }
+    if (!(c->x1 > c->x0) || (c->dim == 2 && !(c->y1 > c->y0))) { set_err(err, "empty domain"); return HGKS_EINVAL; }
+    if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) { set_err(err, "gamma must be > 1"); return HGKS_EINVAL; }
+    if (!(c->fixed_dt > 0.0) && !(c->cfl > 0.0)) { set_err(err, "need cfl > 0 or fixed_dt > 0"); return HGKS_EINVAL; }
+    if (c->viscous && !(c->mu > 0.0)) { set_err(err, "viscous run needs mu > 0"); return HGKS_EINVAL; }
+    if (c->viscous && c->prandtl != 1.0) {
+        set_err(err, "only Pr = 1 (the BGK value of the paper's flux) is supported (got %g)", c->prandtl);
+        return HGKS_EINVAL;
+    }
+    if (c->c1 < 0.0 || c->c2 < 0.0) { set_err(err, "c1, c2 must be >= 0"); return HGKS_EINVAL; }
+    int nb = c->dim == 2 ? 4 : 2;
+    for (int k = 0; k < nb; k++)
+        if (c->bc[k] < HGKS_BC_PERIODIC || c->bc[k] > HGKS_BC_NOSLIP) { set_err(err, "bad boundary type %d", c->bc[k]); return HGKS_EINVAL; }
+    for (int a = 0; a < nb; a += 2)
+        if ((c->bc[a] == HGKS_BC_PERIODIC) != (c->bc[a + 1] == HGKS_BC_PERIODIC)) {
+            set_err(err, "periodic boundaries must be paired on an axis"); return HGKS_EINVAL;
+        }
+    if (c->recon_mode < 0 || c->recon_mode > 2) { set_err(err, "bad recon_mode"); return HGKS_EINVAL; }
+    if (c->zeta1_mode < 0 || c->zeta1_mode > 2) { set_err(err, "bad zeta1_mode"); return HGKS_EINVAL; }
+    if (!(c->gamma_hi > 0.0 && c->gamma_hi < 1.0) || !(c->gamma_lo > 0.0 && c->gamma_lo < 1.0)) {
+        set_err(err, "gamma_hi, gamma_lo must lie in (0, 1)"); return HGKS_EINVAL;
+    }
+    if (!(c->eps > 0.0)) { set_err(err, "eps must be > 0"); return HGKS_EINVAL; }
+    return HGKS_OK;
+}
+
+struct Layout {
+    size_t total;
+    size_t off_W, off_Ws, off_Acc, off_ctrl, off_line, off_gp;
+    size_t off_rawN[2], off_flagN[2], off_rawT[2], off_flagT[2], off_itemsN[2], off_itemsT[2], off_flux[2];
+};
+
+void fill_params(const hgks_config* c, Params& P)
+{
+    memset(&P, 0, sizeof(P));
+    GridGeom& g = P.g;
+    g.dim = c->dim; g.nx = c->nx; g.ny = c->dim == 2 ? c->ny : 1; g.nv = c->dim + 2;
+    g.pitch = (int)align_up((size_t)c->nx + 2 * NG, 4);
+    g.rows = c->dim == 2 ? c->ny + 2 * NG : 1;
+    g.plane = (long long)g.pitch * g.rows;
+    g.origin = (c->dim == 2 ? (long long)NG * g.pitch : 0) + NG;
+    g.dx = (c->x1 - c->x0) / c->nx;
+    g.dy = c->dim == 2 ? (c->y1 - c->y0) / c->ny : 1.0;
+    P.gamma = c->gamma; P.K = dof_K(c->dim, c->gamma); P.mu = c->mu; P.c1 = c->c1; P.c2 = c->c2;
+    P.cfl = c->cfl; P.fixed_dt = c->fixed_dt;
+    P.viscous = c->viscous; P.tau_zero = c->tau_zero; P.recon_mode = c->recon_mode;
+    for (int k = 0; k < 4; k++) P.bc[k] = c->bc[k];
+    double ghi = c->gamma_hi, glo = c->gamma_lo;
+    P.g_ao[3] = ghi;
+    P.g_ao[0] = ((1.0 - ghi) * (1.0 - glo)) * 0.5;
+    P.g_ao[2] = P.g_ao[0];
+    P.g_ao[1] = (1.0 - ghi) * glo;
+    P.g3inv = 1.0 / ghi;
+    for (int j = 0; j < 3; j++) P.gr[j] = P.g_ao[j] / ghi;
+    P.eps = c->eps;
+}
+
+void fill_sweeps(const hgks_config* c, const Params& P, Sweep* sw)
+{
+    const GridGeom& g = P.g;
+    for (int d = 0; d < 2; d++) {
+        Sweep& S = sw[d];
+        memset(&S, 0, sizeof(S));
+        if (d == 1 && c->dim == 1) continue;
+        S.dir = d;
+        S.nn = d == 0 ? g.nx : g.ny;
+        S.nt = c->dim == 2 ? (d == 0 ? g.ny : g.nx) : 1;
+        S.nm = S.nn + 1;
+        S.nlines = c->dim == 2 ? S.nt + 6 : 1;
+        S.tlo = c->dim == 2 ? -3 : 0;
+        S.sN = d == 0 ? 1 : g.pitch;
+        S.sT = d == 0 ? g.pitch : 1;
+        S.perm[0] = 0; S.perm[1] = d == 0 ? 1 : 2; S.perm[2] = d == 0 ? 2 : 1; S.perm[3] = 3;
+        if (c->dim == 1) { S.perm[2] = 2; }
+        double hn = d == 0 ? g.dx : g.dy, ht = d == 0 ? g.dy : g.dx;
+        S.inv12hn = 1.0 / (12.0 * hn);
+        S.inv_hn = 1.0 / hn;
+        S.inv_ht = 1.0 / ht;
+        S.Z1n = zeta1_scaled(c->zeta1_mode, hn);
+        S.Z1t = zeta1_scaled(c->zeta1_mode, ht);
+    }
+}
+
+Layout plan(const hgks_config* c, const Params& P, const Sweep* sw)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    const size_t A = 256;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, A); return o; };
+    size_t st = (size_t)P.g.nv * P.g.plane * sizeof(double);
+    L.off_W = take(st); L.off_Ws = take(st); L.off_Acc = take(st);
+    L.off_ctrl = take(sizeof(Ctrl));
+    int nd = c->dim;
+    size_t maxline = 0, maxgp = 0;
+    for (int d = 0; d < nd; d++) {
+        const Sweep& S = sw[d];
+        maxline = std::max(maxline, (size_t)S.nlines * S.nm);
+        maxgp = std::max(maxgp, (size_t)S.nt * S.nm);
+    }
+    L.off_line = take((size_t)4 * P.g.nv * maxline * sizeof(double));
+    L.off_gp = c->dim == 2 ? take((size_t)2 * 6 * 4 * maxgp * sizeof(double)) : 0;
+    for (int d = 0; d < nd; d++) {
+        const Sweep& S = sw[d];
+        L.off_rawN[d] = take((size_t)S.nlines * (S.nn + 4));
+        L.off_flagN[d] = take((size_t)S.nlines * (S.nn + 2));
+        L.off_itemsN[d] = take((size_t)S.nlines * S.nm * 2 * sizeof(uint32_t));
+        if (c->dim == 2) {
+            L.off_rawT[d] = take((size_t)(S.nt + 2) * S.nm);
+            L.off_flagT[d] = take((size_t)S.nt * S.nm);
+            L.off_itemsT[d] = take((size_t)S.nt * S.nm * 4 * sizeof(uint32_t));
+        }
+        int ngp = c->dim == 2 ? 2 : 1;
+        L.off_flux[d] = take((size_t)ngp * 2 * P.g.nv * S.nt * S.nm * sizeof(double));
+    }
+    L.total = off;
+    return L;
+}
+
+#define CUDA_TRY(s, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_err((s)->err, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+            return HGKS_ECUDA;                                                             \
+        }                                                                                  \
+    } while (0)
+
+int sync_ctrl(hgks_solver* s)
+{
+    CUDA_TRY(s, cudaMemcpyAsync(s->ctrl_host, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return HGKS_OK;
+}
+
+}  // namespace
+
+extern "C" int hgks_config_default(hgks_config* c)
+{
+    if (!c) return HGKS_EINVAL;
+    memset(c, 0, sizeof(*c));
+    c->dim = 2; c->nx = 64; c->ny = 64;
+    c->x0 = 0.0; c->x1 = 1.0; c->y0 = 0.0; c->y1 = 1.0;
+    c->gamma = 1.4; c->viscous = 0; c->mu = 0.0; c->prandtl = 1.0;
+    c->c1 = 0.01; c->c2 = 1.0; c->cfl = 0.5; c->fixed_dt = 0.0; c->tau_zero = 0;
+    for (int k = 0; k < 4; k++) c->bc[k] = HGKS_BC_PERIODIC;
+    c->recon_mode = HGKS_RECON_HYBRID; c->zeta1_mode = HGKS_ZETA1_B;
+    c->gamma_hi = 0.85; c->gamma_lo = 0.85; c->eps = 1e-8;
+    return HGKS_OK;
+}
+
+extern "C" size_t hgks_footprint_bytes(const hgks_config* cfg)
+{
+    char err[512];
+    if (validate(cfg, err) != HGKS_OK) return 0;
+    Params P; Sweep sw[2];
+    fill_params(cfg, P);
+    fill_sweeps(cfg, P, sw);
+    return plan(cfg, P, sw).total;
+}
+
+extern "C" int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_solver** out)
+{
+    if (!out) { set_err(g_create_err, "out is NULL"); return HGKS_EINVAL; }
+    *out = nullptr;
+    int st = validate(cfg, g_create_err);
+    if (st != HGKS_OK) return st;
+    hgks_solver* s = new (std::nothrow) hgks_solver();
+    if (!s) { set_err(g_create_err, "host allocation failed"); return HGKS_ENOMEM; }
+    s->cfg = *cfg;
+    s->stream = (cudaStream_t)stream;
+    s->err[0] = 0;
+    cudaGetDevice(&s->device);
+    fill_params(cfg, s->P);
+    fill_sweeps(cfg, s->P, s->sw);
+    Layout L = plan(cfg, s->P, s->sw);
+    cudaError_t e = cudaMalloc(&s->pool, L.total);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+        delete s;
+        return e == cudaErrorMemoryAllocation ? HGKS_ENOMEM : HGKS_ECUDA;
+    }
+    s->pool_bytes = L.total;
+    e = cudaMallocHost(&s->ctrl_host, sizeof(Ctrl));
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+        cudaFree(s->pool); delete s; return HGKS_ENOMEM;
+    }
+    char* base = (char*)s->pool;
+    s->W = (double*)(base + L.off_W);
+    s->Ws = (double*)(base + L.off_Ws);
+    s->Acc = (double*)(base + L.off_Acc);
+    s->ctrl = (Ctrl*)(base + L.off_ctrl);
+    for (int d = 0; d < cfg->dim; d++) {
+        Sweep& S = s->sw[d];
+        S.line = (double*)(base + L.off_line);
+        S.gp = cfg->dim == 2 ? (double*)(base + L.off_gp) : nullptr;
+        S.rawN = (uint8_t*)(base + L.off_rawN[d]);
+        S.flagN = (uint8_t*)(base + L.off_flagN[d]);
+        S.itemsN = (uint32_t*)(base + L.off_itemsN[d]);
+        if (cfg->dim == 2) {
+            S.rawT = (uint8_t*)(base + L.off_rawT[d]);
+            S.flagT = (uint8_t*)(base + L.off_flagT[d]);
+            S.itemsT = (uint32_t*)(base + L.off_itemsT[d]);
+        }
+        S.flux = (double*)(base + L.off_flux[d]);
+    }
+    memset(s->cap, 0, sizeof(s->cap));
+    s->capture = 0;
+    s->launches = 0;
+    s->timing = 0;
+    s->timer_ms.assign(KC_COUNT, 0.0);
+    s->timer_calls.assign(KC_COUNT, 0);
+    e = cudaMemsetAsync(s->pool, 0, L.total, s->stream);
+    if (e == cudaSuccess) e = launch_set_time(s, 0.0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "initialisation failed: %s", cudaGetErrorString(e));
+        cudaFreeHost(s->ctrl_host); cudaFree(s->pool); delete s;
+        return HGKS_ECUDA;
+    }
+    *out = s;
+    return HGKS_OK;
+}
+
+extern "C" void hgks_destroy_solver(hgks_solver* s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (auto& r : s->timers) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : s->event_pool) cudaEventDestroy(e);
+    for (int a = 0; a < 2; a++) for (int b = 0; b < 2; b++) for (int c = 0; c < 2; c++)
+        if (s->cap[a][b][c]) cudaFree(s->cap[a][b][c]);
+    cudaFreeHost(s->ctrl_host);
+    cudaFree(s->pool);
+    delete s;
+}
+
+extern "C" const char* hgks_last_error(const hgks_solver* s)
+{
+    return s ? s->err : g_create_err;
+}
+
+extern "C" int hgks_set_state(hgks_solver* s, const double* W, int on_device, double t0)
+{
+    if (!s || !W) return HGKS_EINVAL;
+    const GridGeom& g = s->P.g;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int k = 0; k < g.nv; k++) {
+        CUDA_TRY(s, cudaMemcpy2DAsync(s->W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
+                                      W + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),
+                                      (size_t)g.nx * sizeof(double), (size_t)g.ny, kind, s->stream));
+    }
+    CUDA_TRY(s, launch_set_time(s, t0));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    s->launches = 0;
+    return HGKS_OK;
+}
+
+extern "C" int hgks_get_state(hgks_solver* s, double* W, int on_device)
+{
+    if (!s || !W) return HGKS_EINVAL;
+    const GridGeom& g = s->P.g;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < g.nv; k++) {
+        CUDA_TRY(s, cudaMemcpy2DAsync(W + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),
+                                      s->W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
+                                      (size_t)g.nx * sizeof(double), (size_t)g.ny, kind, s->stream));
+    }
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return HGKS_OK;
+}
+
+extern "C" int hgks_step(hgks_solver* s, double t_end, int max_steps, int* steps_done)
+{
+    if (!s || max_steps < 0 || !std::isfinite(t_end)) return HGKS_EINVAL;
+    if (!steps_done) {
+        for (int n = 0; n < max_steps; n++) CUDA_TRY(s, launch_step(s, t_end));
+        return HGKS_OK;
+    }
+    int st = sync_ctrl(s);
+    if (st != HGKS_OK) return st;
+    long long steps0 = s->ctrl_host->steps;
+    int left = max_steps, chunk = 8;
+    while (left > 0 && !s->ctrl_host->status) {
+        int n = left < chunk ? left : chunk;
+        for (int k = 0; k < n; k++) CUDA_TRY(s, launch_step(s, t_end));
+        left -= n;
+        st = sync_ctrl(s);
+        if (st != HGKS_OK) return st;
+        if (s->ctrl_host->done) break;
+        if (chunk < 512) chunk *= 2;
+    }
+    *steps_done = (int)(s->ctrl_host->steps - steps0);
+    if (s->ctrl_host->status) {
+        set_err(s->err, "non-physical state (rho <= 0, p <= 0 or non-finite) detected at t = %.17g", s->ctrl_host->t);
+        return s->ctrl_host->status;
+    }
+    return HGKS_OK;
+}
+
+extern "C" int hgks_get_time(hgks_solver* s, double* t)
+{
+    if (!s || !t) return HGKS_EINVAL;
+    int st = sync_ctrl(s);
+    if (st != HGKS_OK) return st;
+    *t = s->ctrl_host->t;
+    return HGKS_OK;
+}
+
+extern "C" int hgks_get_stats(hgks_solver* s, hgks_stats* out)
+{
+    if (!s || !out) return HGKS_EINVAL;
+    int st = sync_ctrl(s);
+    if (st != HGKS_OK) return st;
+    const Ctrl& c = *s->ctrl_host;
+    memset(out, 0, sizeof(*out));
+    out->steps = c.steps; out->t = c.t; out->last_dt = c.last_dt; out->status = c.status;
+    out->launches = s->launches;
+    for (int a = 0; a < 2; a++) for (int b = 0; b < 2; b++) for (int k = 0; k < 2; k++) {
+        out->troubled[a][b][k] = (long long)c.troubled[a][b][k];
+        out->examined[a][b][k] = (long long)c.examined[a][b][k];
+    }
+    return HGKS_OK;
+}
+
+extern "C" size_t hgks_flags_size(const hgks_solver* s, int sweep, int kind)
+{
+    if (!s || sweep < 0 || sweep >= s->cfg.dim || kind < 0 || kind > 1) return 0;
+    const Sweep& S = s->sw[sweep];
+    if (kind == 0) return (size_t)S.nlines * (S.nn + 2);
+    if (s->cfg.dim == 1) return 0;
+    return (size_t)S.nt * S.nm;
+}
+
+extern "C" int hgks_set_flag_capture(hgks_solver* s, int enable)
+{
+    if (!s) return HGKS_EINVAL;
+    if (enable) {
+        for (int a = 0; a < 2; a++) for (int d = 0; d < s->cfg.dim; d++) for (int k = 0; k < 2; k++) {
+            size_t n = hgks_flags_size(s, d, k);
+            if (n && !s->cap[a][d][k]) {
+                CUDA_TRY(s, cudaMalloc(&s->cap[a][d][k], n));
+                CUDA_TRY(s, cudaMemsetAsync(s->cap[a][d][k], 0, n, s->stream));
+            }
+        }
+    }
+    s->capture = enable ? 1 : 0;
+    return HGKS_OK;
+}
+
+extern "C" int hgks_get_flags(hgks_solver* s, int stage, int sweep, int kind, uint8_t* out)
+{
+    if (!s || !out || stage < 0 || stage > 1) return HGKS_EINVAL;
+    size_t n = hgks_flags_size(s, sweep, kind);
+    if (!n || !s->cap[stage][sweep][kind]) { set_err(s->err, "flags not captured (enable capture first)"); return HGKS_EINVAL; }
+    CUDA_TRY(s, cudaMemcpyAsync(out, s->cap[stage][sweep][kind], n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return HGKS_OK;
+}
+
+extern "C" int hgks_set_timing(hgks_solver* s, int enable)
+{
+    if (!s) return HGKS_EINVAL;
+    s->timing = enable ? 1 : 0;
+    return HGKS_OK;
+}
+
+extern "C" int hgks_get_timing(hgks_solver* s, int cap, const char** names, double* ms, long long* calls)
+{
+    if (!s) return HGKS_EINVAL;
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    for (auto& r : s->timers) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            s->timer_ms[r.cls] += t;
+            s->timer_calls[r.cls] += 1;
+        }
+        s->event_pool.push_back(r.a);
+        s->event_pool.push_back(r.b);
+    }
+    s->timers.clear();
+    int n = 0;
+    for (int k = 0; k < KC_COUNT && n < cap; k++) {
+        if (names) names[n] = kclass_names[k];
+        if (ms) ms[n] = s->timer_ms[k];
+        if (calls) calls[n] = s->timer_calls[k];
+        n++;
+    }
+    return n;
+}
+
+extern "C" int hgks_batch_step(hgks_solver* const* solvers, int n, const double* t_end, void* stream)
+{
+    if (n < 0 || (n > 0 && (!solvers || !t_end))) return HGKS_EINVAL;
+    cudaStream_t bs = (cudaStream_t)stream;
+    for (int i = 0; i < n; i++) {
+        hgks_solver* s = solvers[i];
+        if (!s) return HGKS_EINVAL;
+        cudaEvent_t e;
+        CUDA_TRY(s, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CUDA_TRY(s, cudaEventRecord(e, s->stream));
+        CUDA_TRY(s, cudaStreamWaitEvent(bs, e, 0));
+        cudaStream_t own = s->stream;
+        s->stream = bs;
+        cudaError_t err = launch_step(s, t_end[i]);
+        s->stream = own;
+        if (err != cudaSuccess) { cudaEventDestroy(e); set_err(s->err, "launch failed: %s", cudaGetErrorString(err)); return HGKS_ECUDA; }
+        CUDA_TRY(s, cudaEventRecord(e, bs));
+        CUDA_TRY(s, cudaStreamWaitEvent(own, e, 0));
+        cudaEventDestroy(e);
+    }
+    return HGKS_OK;
+}

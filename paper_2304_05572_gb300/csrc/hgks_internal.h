@@ -1,0 +1,109 @@
+// hgks_internal.h -- private declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hgks.h"
+
+namespace hgks {
+
+constexpr int NG = 4;            // ghost layers: the widest stencil (a Step-4 spread of 5-cell tests) reaches 4 cells
+constexpr int MAXNV = 4;
+
+// Device control block of one solver: time, dt, status and counters.  All
+// step logic that would otherwise need a host round trip lives here.
+struct Ctrl {
+    double t;
+    double dt;
+    double last_dt;
+    unsigned long long dtmin_bits;   // atomicMin over positive doubles as ordered integers
+    int done;                        // 1: the current step does nothing (t reached t_end or error latched)
+    int status;                      // 0 or HGKS_ENONPHYSICAL
+    long long steps;
+    unsigned int cnt[2][2];          // AO work-list lengths [sweep][0 normal, 1 tangential]
+    unsigned long long troubled[2][2][2];
+    unsigned long long examined[2][2][2];
+};
+
+struct GridGeom {
+    int dim, nx, ny, nv;
+    int pitch;                 // padded row length in doubles (nx + 2 NG rounded up)
+    int rows;                  // padded rows (ny + 2 NG in 2D, 1 in 1D)
+    long long plane;           // pitch * rows
+    long long origin;          // offset of interior cell (0, 0)
+    double dx, dy;
+};
+
+// One sweep in its local frame: n = index normal to the interfaces, t = tangential index.
+struct Sweep {
+    int dir;                   // 0: x-interfaces, 1: y-interfaces
+    int nn, nt;                // cells normal / tangential
+    int nm;                    // interfaces per line (nn + 1)
+    int nlines;                // lines with normal reconstruction (nt + 6 in 2D, 1 in 1D)
+    int tlo;                   // first line index (-3 in 2D, 0 in 1D)
+    long long sN, sT;          // state strides for +1 in n / t
+    int perm[4];               // local component -> global component
+    double inv12hn, inv_hn, inv_ht, Z1n, Z1t;
+    uint8_t* rawN;             // [nlines][nn + 4]   raw normal flags, cells -2..nn+1
+    uint8_t* flagN;            // [nlines][nn + 2]   final normal flags, cells -1..nn
+    double* line;              // [4][nv][nlines][nm] Q^l, Q^r, Q^l_n, Q^r_n
+    uint8_t* rawT;             // [nt + 4][nm]       raw tangential flag bits, lines -2..nt+1
+    uint8_t* flagT;            // [nt][nm]           final tangential flag bits
+    double* gp;                // [2][6][nv][nt][nm] Gauss-point states
+    double* flux;              // [ngp][2][nv][nt][nm] per-Gauss-point flux outputs (global order)
+    uint32_t* itemsN;          // AO work list, normal pass
+    uint32_t* itemsT;          // AO work list, tangential passes
+};
+
+struct Params {
+    GridGeom g;
+    double gamma, K, mu, c1, c2, cfl, fixed_dt;
+    int viscous, tau_zero, recon_mode;
+    int bc[4];
+    double g_ao[4], g3inv, gr[3], eps;
+};
+
+struct TimerRec { int cls; cudaEvent_t a, b; };
+
+}  // namespace hgks
+
+struct hgks_solver {
+    hgks_config cfg;
+    hgks::Params P;
+    cudaStream_t stream;
+    int device;
+    hgks::Sweep sw[2];
+    double* W;       // padded state W^n (and W^{n+1})
+    double* Ws;      // padded W*
+    double* Acc;     // padded accumulator of stage 1
+    hgks::Ctrl* ctrl;        // device
+    hgks::Ctrl* ctrl_host;   // pinned mirror
+    void* pool;              // single device allocation holding all buffers
+    size_t pool_bytes;
+    uint8_t* cap[2][2][2];   // captured flags [stage][sweep][kind]
+    int capture;
+    long long launches;      // kernels enqueued since set_state (host count)
+    int timing;
+    std::vector<hgks::TimerRec> timers;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<double> timer_ms;
+    std::vector<long long> timer_calls;
+    char err[512];
+};
+
+namespace hgks {
+
+// kernel classes for timing
+enum KClass { KC_GHOST = 0, KC_DT, KC_RAWN, KC_NORMAL, KC_NORMAL_AO, KC_RAWT, KC_TANG, KC_TANG_AO, KC_FLUX, KC_UPDATE, KC_MISC, KC_COUNT };
+extern const char* kclass_names[KC_COUNT];
+
+// host-side launchers (hgks_kernels.cu); all enqueue on s->stream
+cudaError_t launch_step(hgks_solver* s, double t_end);
+cudaError_t launch_set_time(hgks_solver* s, double t0);
+int device_sm_count();
+
+}  // namespace hgks

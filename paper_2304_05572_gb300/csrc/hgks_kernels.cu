@@ -1,0 +1,707 @@
+// hgks_kernels.cu -- the S2O4 step of the hybrid WENO-AO gas-kinetic scheme as sm_103a
+// FP64 kernels (arXiv 2304.05572, Sec. 2), and the host code that enqueues one step.
+//
+// Per stage: ghost fill -> for each sweep (x, then y in 2D):
+//   raw normal flags -> normal reconstruction (linear inline, troubled sides appended to a
+//   work list with warp-aggregated atomics) -> dense WENO-AO pass over that list ->
+//   [2D: raw tangential flags -> Gauss-point reconstruction (linear inline, troubled passes
+//   compacted the same way) -> dense WENO-AO pass] -> gas-kinetic flux per Gauss point
+// -> stage update.  dt is reduced, clipped to t_end and applied on the device.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "hgks_internal.h"
+#include "hgks_math.cuh"
+
+namespace hgks {
+
+const char* kclass_names[KC_COUNT] = {"ghost", "dt", "raw_normal_flags", "normal_recon", "normal_weno_ao",
+                                      "raw_tangential_flags", "tangential_recon", "tangential_weno_ao",
+                                      "gks_flux", "stage_update", "misc"};
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------- ghost cells
+// x ghosts on interior rows, then y ghosts over the padded width (fills corners).
+// Non-reflecting: zero-gradient copy; reflect / symmetry: mirror, normal momentum negated;
+// no-slip adiabatic: mirror, both momenta negated.
+__global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    const GridGeom& g = P.g;
+    int rowsI = g.dim == 2 ? g.ny : 1;
+    long long total = (long long)g.nv * rowsI * NG * 2;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    int side = (int)(id % 2); id /= 2;
+    int l = (int)(id % NG) + 1; id /= NG;
+    int j = (int)(id % rowsI);
+    int k = (int)(id / rowsI);
+    int bc = P.bc[side];
+    int dst = side == 0 ? -l : g.nx - 1 + l;
+    int src;
+    bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP;
+    if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.nx - l : l - 1;
+    else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.nx - 1;
+    else src = side == 0 ? l - 1 : g.nx - l;
+    double* base = W + g.origin + (long long)k * g.plane + (long long)j * g.pitch;
+    double v = base[src];
+    if (mirror) {
+        if (k == 1) v = -v;
+        if (bc == HGKS_BC_NOSLIP && g.dim == 2 && k == 2) v = -v;
+    }
+    base[dst] = v;
+}
+
+__global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    const GridGeom& g = P.g;
+    int width = g.nx + 2 * NG;
+    long long total = (long long)g.nv * width * NG * 2;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    int i = (int)(id % width) - NG; id /= width;
+    int side = (int)(id % 2); id /= 2;
+    int l = (int)(id % NG) + 1;
+    int k = (int)(id / NG);
+    int bc = P.bc[2 + side];
+    int dst = side == 0 ? -l : g.ny - 1 + l;
+    int src;
+    bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP;
+    if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.ny - l : l - 1;
+    else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.ny - 1;
+    else src = side == 0 ? l - 1 : g.ny - l;
+    double* base = W + g.origin + (long long)k * g.plane + i;
+    double v = base[(long long)src * g.pitch];
+    if (mirror) {
+        if (k == 2) v = -v;
+        if (bc == HGKS_BC_NOSLIP && k == 1) v = -v;
+    }
+    base[(long long)dst * g.pitch] = v;
+}
+
+// ---------------------------------------------------------------- time step
+__global__ void k_begin_step(Ctrl* ctrl)
+{
+    ctrl->dtmin_bits = 0x7FF0000000000000ull;   // +inf
+    ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
+}
+
+__global__ void k_begin_stage(Ctrl* ctrl)
+{
+    ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
+}
+
+// Sec. 3 preamble: dt = CFL min(h/(|U|+a), h^2/(4 nu)), h = min(dx, dy), nu = mu/rho;
+// same evaluation order as the CPU reference so that dt is reproduced exactly.
+__global__ void k_dt(Params P, const double* __restrict__ W, Ctrl* ctrl, double h)
+{
+    const GridGeom& g = P.g;
+    int rowsI = g.dim == 2 ? g.ny : 1;
+    long long n = (long long)rowsI * g.nx;
+    unsigned long long best = 0x7FF0000000000000ull;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        const double* c = W + g.origin + (long long)j * g.pitch + i;
+        ex rho(c[0]);
+        ex ri = ex(1.0) / rho;
+        ex U = ex(c[g.plane]) * ri;
+        ex V = g.dim == 2 ? ex(c[2 * g.plane]) * ri : ex(0.0);
+        ex q2 = U * U + V * V;
+        ex p = (ex(P.gamma) - ex(1.0)) * (ex(c[(g.nv - 1) * g.plane]) - (ex(0.5) * rho) * q2);
+        ex a = xsqrt((ex(P.gamma) * p) * ri);
+        ex d = ex(h) / (xsqrt(q2) + a);
+        if (P.viscous) {
+            ex nu = ex(P.mu) * ri;
+            ex dv = (ex(h) * ex(h)) / (ex(4.0) * nu);
+            if (dv.v < d.v) d = dv;
+        }
+        unsigned long long bits = (unsigned long long)__double_as_longlong(d.v);
+        if (!(d.v > 0.0)) bits = 0x7FF8000000000000ull;   // non-physical cells are caught by the update
+        best = bits < best ? bits : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(&ctrl->dtmin_bits, best);
+}
+
+__global__ void k_dt_final(Ctrl* ctrl, double cfl, double fixed_dt, double t_end, double tol)
+{
+    double dt = fixed_dt > 0.0 ? fixed_dt : cfl * __longlong_as_double((long long)ctrl->dtmin_bits);
+    int done = ctrl->status != 0 || !(t_end - ctrl->t > tol);
+    if (!done && ctrl->t + dt > t_end) dt = t_end - ctrl->t;
+    if (!done && !(dt > 0.0 && dt < 1e300)) { ctrl->status = HGKS_ENONPHYSICAL; done = 1; }
+    ctrl->dt = dt;
+    ctrl->done = done;
+}
+
+__global__ void k_end_step(Ctrl* ctrl)
+{
+    if (ctrl->done) return;
+    ctrl->t += ctrl->dt;
+    ctrl->last_dt = ctrl->dt;
+    ctrl->steps += 1;
+}
+
+__global__ void k_set_time(Ctrl* ctrl, double t0)
+{
+    ctrl->t = t0;
+    ctrl->dt = 0.0;
+    ctrl->last_dt = 0.0;
+    ctrl->steps = 0;
+    ctrl->status = 0;
+    ctrl->done = 0;
+    for (int a = 0; a < 2; a++) for (int b = 0; b < 2; b++) for (int c = 0; c < 2; c++) {
+        ctrl->troubled[a][b][c] = 0; ctrl->examined[a][b][c] = 0;
+    }
+}
+
+// warp-aggregated counter add
+__device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned int v)
+{
+    unsigned int tot = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(dst, (unsigned long long)tot);
+}
+
+// warp-aggregated append of one item per set predicate; returns nothing, writes list
+__device__ __forceinline__ void warp_push(unsigned int* cnt, uint32_t* list, bool pred, uint32_t item)
+{
+    unsigned int mask = __ballot_sync(0xffffffffu, pred);
+    if (!mask) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (unsigned int)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
+// ---------------------------------------------------------------- normal pass
+// local state access: component k of cell n on line t
+__device__ __forceinline__ const double* cellp(const Params& P, const Sweep& S, const double* W, int t, int n)
+{
+    return W + P.g.origin + (long long)t * S.sT + (long long)n * S.sN;
+}
+
+template <int NV>
+__global__ void k_raw_nflags(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    int width = S.nn + 4;
+    long long total = (long long)S.nlines * width;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    int c = (int)(id % width), L = (int)(id / width);
+    int t = L + S.tlo, n = c - 2;
+    int tr = 0;
+    if (P.recon_mode == HGKS_RECON_HYBRID) {
+        const double* base = cellp(P, S, W, t, n - 2);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double q[5];
+            const double* b = base + (long long)S.perm[k] * P.g.plane;
+#pragma unroll
+            for (int s = 0; s < 5; s++) q[s] = ld(b + (long long)s * S.sN);
+            tr |= indicator_raw(q, S.Z1n);
+        }
+    }
+    S.rawN[id] = (uint8_t)tr;
+}
+
+template <int NV>
+__device__ __forceinline__ void store_line(const Params& P, const Sweep& S, int L, int m, int side, const double* val, const double* der)
+{
+    long long plane = (long long)S.nlines * S.nm;
+    long long o = (long long)L * S.nm + m;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        S.line[(long long)(side * NV + k) * plane + o] = val[k];
+        S.line[(long long)((2 + side) * NV + k) * plane + o] = der[k];
+    }
+}
+
+template <int NV>
+__global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* ctrl, int stage)
+{
+    if (ctrl->done) return;
+    long long total = (long long)S.nlines * S.nm;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = id < total;
+    int L = 0, m = 0;
+    if (active) { m = (int)(id % S.nm); L = (int)(id / S.nm); }
+    int t = L + S.tlo;
+    int fl[2] = {0, 0};
+    if (active) {
+        const uint8_t* raw = S.rawN + (long long)L * (S.nn + 4);
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            int c = m - 1 + side;     // cell index; raw index of cell c is c + 2
+            int f;
+            if (P.recon_mode == HGKS_RECON_LINEAR) f = 0;
+            else if (P.recon_mode == HGKS_RECON_WENOAO) f = 1;
+            else f = raw[c + 1] | raw[c + 2] | raw[c + 3];          // Step 4
+            fl[side] = f;
+        }
+        uint8_t* fo = S.flagN + (long long)L * (S.nn + 2);
+        fo[m + 1] = (uint8_t)fl[1];
+        if (m == 0) fo[0] = (uint8_t)fl[0];
+    }
+    bool counted = active && t >= 0 && t < S.nt && m < S.nn;
+    warp_count(&ctrl->troubled[stage][S.dir][0], counted && fl[1] ? 1u : 0u);
+    warp_count(&ctrl->examined[stage][S.dir][0], counted ? 1u : 0u);
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        bool push = active && fl[side];
+        warp_push(&ctrl->cnt[S.dir][0], S.itemsN, push, (uint32_t)((((long long)L * S.nm + m) << 1) | side));
+        if (!active || fl[side]) continue;
+        int c = m - 1 + side;
+        double val[NV], der[NV];
+        const double* base = cellp(P, S, W, t, c - 2);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double q[5];
+            const double* b = base + (long long)S.perm[k] * P.g.plane;
+#pragma unroll
+            for (int s = 0; s < 5; s++) q[s] = ld(b + (long long)s * S.sN);
+            if (side == 0) linear_left(q, S.inv12hn, val[k], der[k]);
+            else linear_right(q, S.inv12hn, val[k], der[k]);
+        }
+        if (nonphysical<NV>(P.gamma, val)) {
+            const double* cc = cellp(P, S, W, t, c);
+#pragma unroll
+            for (int k = 0; k < NV; k++) { val[k] = ld(cc + (long long)S.perm[k] * P.g.plane); der[k] = 0.0; }
+        }
+        store_line<NV>(P, S, L, m, side, val, der);
+    }
+}
+
+template <int NV>
+__global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    unsigned int n = ctrl->cnt[S.dir][0];
+    AOConst ak;
+    for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
+    ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t it = S.itemsN[i];
+        int side = it & 1;
+        long long lm = it >> 1;
+        int m = (int)(lm % S.nm), L = (int)(lm / S.nm);
+        int t = L + S.tlo;
+        int c = m - 1 + side;
+        double Qw[5][NV], Qs[NV], val[NV], d[NV], der[NV];
+        const double* base = cellp(P, S, W, t, c - 2);
+#pragma unroll
+        for (int s = 0; s < 5; s++)
+#pragma unroll
+            for (int k = 0; k < NV; k++) Qw[s][k] = ld(base + (long long)s * S.sN + (long long)S.perm[k] * P.g.plane);
+        const double* cl = cellp(P, S, W, t, m - 1);
+        const double* cr = cellp(P, S, W, t, m);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            long long o = (long long)S.perm[k] * P.g.plane;
+            Qs[k] = ((ex(ld(cl + o)) + ex(ld(cr + o))) * ex(0.5)).v;
+        }
+        weno_ao_face<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, val, d);
+#pragma unroll
+        for (int k = 0; k < NV; k++) der[k] = (ex(d[k]) * ex(S.inv_hn)).v;
+        if (nonphysical<NV>(P.gamma, val)) {
+#pragma unroll
+            for (int k = 0; k < NV; k++) { val[k] = Qw[2][k]; der[k] = 0.0; }
+        }
+        store_line<NV>(P, S, L, m, side, val, der);
+    }
+}
+
+// ---------------------------------------------------------------- tangential passes (2D)
+__device__ __forceinline__ double lineval(const Sweep& S, int X, int k, int t, int m)
+{
+    long long plane = (long long)S.nlines * S.nm;
+    return ld(S.line + (long long)(X * 4 + k) * plane + (long long)(t - S.tlo) * S.nm + m);
+}
+
+__global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    long long total = (long long)(S.nt + 2) * S.nm;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    int m = (int)(id % S.nm);
+    int t = (int)(id / S.nm) - 1;
+    uint8_t bits = 0;
+    if (P.recon_mode == HGKS_RECON_HYBRID) {
+#pragma unroll
+        for (int X = 0; X < 4; X++) {
+            int tr = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                double q[5];
+#pragma unroll
+                for (int s = 0; s < 5; s++) q[s] = lineval(S, X, k, t - 2 + s, m);
+                tr |= indicator_raw(q, S.Z1t);
+            }
+            bits |= (uint8_t)(tr << X);
+        }
+    }
+    S.rawT[id] = bits;
+}
+
+__device__ __forceinline__ void store_gp(const Sweep& S, int t, int m, int X, const double (*v)[2], const double (*d)[2], double inv_ht)
+{
+    long long plane = (long long)S.nt * S.nm;
+    long long o = (long long)t * S.nm + m;
+    // Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry
+    int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
+#pragma unroll
+    for (int g = 0; g < 2; g++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            S.gp[(long long)((g * 6 + qv) * 4 + k) * plane + o] = v[k][g];
+            if (X <= 1) S.gp[(long long)((g * 6 + qv + 2) * 4 + k) * plane + o] = d[k][g] * inv_ht;
+        }
+}
+
+__device__ __forceinline__ void gp_positivity(const Params& P, const Sweep& S, int t, int m, int X, double (*v)[2], double (*d)[2])
+{
+    if (X > 1) return;
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        double Q[4] = {v[0][g], v[1][g], v[2][g], v[3][g]};
+        if (nonphysical<4>(P.gamma, Q)) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) { v[k][g] = lineval(S, X, k, t, m); d[k][g] = 0.0; }
+        }
+    }
+}
+
+__global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
+{
+    if (ctrl->done) return;
+    long long total = (long long)S.nt * S.nm;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = id < total;
+    int m = 0, t = 0;
+    unsigned int bits = 0;
+    if (active) {
+        m = (int)(id % S.nm); t = (int)(id / S.nm);
+        if (P.recon_mode == HGKS_RECON_LINEAR) bits = 0;
+        else if (P.recon_mode == HGKS_RECON_WENOAO) bits = 0xF;
+        else bits = S.rawT[(long long)t * S.nm + m] | S.rawT[(long long)(t + 1) * S.nm + m] | S.rawT[(long long)(t + 2) * S.nm + m];
+        S.flagT[id] = (uint8_t)bits;
+    }
+    warp_count(&ctrl->troubled[stage][S.dir][1], active ? (unsigned)__popc(bits) : 0u);
+    warp_count(&ctrl->examined[stage][S.dir][1], active ? 4u : 0u);
+#pragma unroll
+    for (int X = 0; X < 4; X++) {
+        bool f = active && ((bits >> X) & 1);
+        warp_push(&ctrl->cnt[S.dir][1], S.itemsT, f, (uint32_t)((((long long)t * S.nm + m) << 2) | X));
+        if (!active || f) continue;
+        double v[4][2], d[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double q[5];
+#pragma unroll
+            for (int s = 0; s < 5; s++) q[s] = lineval(S, X, k, t - 2 + s, m);
+            gauss_linear(q, v[k], d[k]);
+        }
+        gp_positivity(P, S, t, m, X, v, d);
+        store_gp(S, t, m, X, v, d, S.inv_ht);
+    }
+}
+
+__global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    if (ctrl->done) return;
+    unsigned int n = ctrl->cnt[S.dir][1];
+    AOConst ak;
+    for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
+    ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t it = S.itemsT[i];
+        int X = it & 3;
+        long long tm = it >> 2;
+        int m = (int)(tm % S.nm), t = (int)(tm / S.nm);
+        ex qs[4], Lm[4][4], Rm[4][4], Uc[5][4];
+        const double* cl = cellp(P, S, W, t, m - 1);
+        const double* cr = cellp(P, S, W, t, m);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            long long o = (long long)S.perm[k] * P.g.plane;
+            qs[k] = (ex(ld(cl + o)) + ex(ld(cr + o))) * ex(0.5);
+        }
+        eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            ex x[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) x[k] = ex(lineval(S, X, k, t - 2 + s, m));
+            matvec<4>(Lm, x, Uc[s]);
+        }
+        double cv[4][2], cd[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            ex q[5];
+#pragma unroll
+            for (int s = 0; s < 5; s++) q[s] = Uc[s][k];
+            gauss_ao(q, ak, cv[k], cd[k]);
+        }
+        double v[4][2], d[4][2];
+#pragma unroll
+        for (int g = 0; g < 2; g++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                double a = 0.0, b = 0.0;
+#pragma unroll
+                for (int c = 0; c < 4; c++) { a = fma(Rm[r][c].v, cv[c][g], a); b = fma(Rm[r][c].v, cd[c][g], b); }
+                v[r][g] = a; d[r][g] = b;
+            }
+        gp_positivity(P, S, t, m, X, v, d);
+        store_gp(S, t, m, X, v, d, S.inv_ht);
+    }
+}
+
+// ---------------------------------------------------------------- flux and update
+template <int DIM, int STAGE>
+__global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
+{
+    if (ctrl->done) return;
+    constexpr int NV = DIM + 2;
+    constexpr int NGP = DIM == 2 ? 2 : 1;
+    long long per = (long long)S.nt * S.nm;
+    long long total = per * NGP;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    int g = (int)(id / per);
+    long long o = id % per;
+    double Wq[6][NV];
+    if constexpr (DIM == 2) {
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+#pragma unroll
+            for (int k = 0; k < NV; k++) Wq[q][k] = ld(S.gp + (long long)((g * 6 + q) * 4 + k) * per + o);
+    } else {
+        long long plane = (long long)S.nlines * S.nm;
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            Wq[0][k] = ld(S.line + (long long)(0 * NV + k) * plane + o);
+            Wq[1][k] = ld(S.line + (long long)(2 * NV + k) * plane + o);
+            Wq[3][k] = ld(S.line + (long long)(1 * NV + k) * plane + o);
+            Wq[4][k] = ld(S.line + (long long)(3 * NV + k) * plane + o);
+            Wq[2][k] = 0.0; Wq[5][k] = 0.0;
+        }
+    }
+    FluxConst fc{P.gamma, P.K, P.mu, P.c1, P.c2, P.viscous, P.tau_zero};
+    double o0[NV], o1[NV];
+    bool ok = gks_flux<DIM, STAGE>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1);
+    if (!ok) { ctrl->status = HGKS_ENONPHYSICAL; return; }
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        int gk = S.perm[k];
+        S.flux[(long long)((g * 2 + 0) * NV + gk) * per + o] = o0[k];
+        if (STAGE == 0) S.flux[(long long)((g * 2 + 1) * NV + gk) * per + o] = o1[k];
+    }
+}
+
+// Stage 0: W* = W^n - dF(dt/2)/dx - dG(dt/2)/dy (Eq. (19)), Acc = W^n - d(dt F^n + dt^2/6 dF^n)/dx - ...
+// Stage 1: W^{n+1} = Acc - d(dt^2/3 dF*)/dx - ... (Eqs. (20)-(22))
+template <int DIM, int STAGE>
+__global__ void k_update(Params P, Sweep Sx, Sweep Sy, const double* __restrict__ Win, double* __restrict__ Wout,
+                         double* __restrict__ Acc, Ctrl* ctrl)
+{
+    if (ctrl->done) return;
+    constexpr int NV = DIM + 2;
+    const GridGeom& g = P.g;
+    int rowsI = DIM == 2 ? g.ny : 1;
+    long long n = (long long)rowsI * g.nx;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    long long cell = g.origin + (long long)j * g.pitch + i;
+    const double inv_dx = 1.0 / g.dx, inv_dy = DIM == 2 ? 1.0 / g.dy : 0.0;
+    long long perx = (long long)Sx.nt * Sx.nm, pery = DIM == 2 ? (long long)Sy.nt * Sy.nm : 0;
+    long long ox = (long long)j * Sx.nm + i, oy = (long long)i * (DIM == 2 ? Sy.nm : 0) + j;
+    double out[NV], acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double fx0[2], fx1[2], fy0[2] = {0, 0}, fy1[2] = {0, 0};
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const double* fb = Sx.flux;
+            if constexpr (DIM == 2) {
+                fx0[s] = 0.5 * ld(fb + (long long)((0 * 2 + 0) * NV + k) * perx + ox + s) + 0.5 * ld(fb + (long long)((1 * 2 + 0) * NV + k) * perx + ox + s);
+                fx1[s] = STAGE == 0 ? 0.5 * ld(fb + (long long)((0 * 2 + 1) * NV + k) * perx + ox + s) + 0.5 * ld(fb + (long long)((1 * 2 + 1) * NV + k) * perx + ox + s) : 0.0;
+                const double* gb = Sy.flux;
+                fy0[s] = 0.5 * ld(gb + (long long)((0 * 2 + 0) * NV + k) * pery + oy + s) + 0.5 * ld(gb + (long long)((1 * 2 + 0) * NV + k) * pery + oy + s);
+                fy1[s] = STAGE == 0 ? 0.5 * ld(gb + (long long)((0 * 2 + 1) * NV + k) * pery + oy + s) + 0.5 * ld(gb + (long long)((1 * 2 + 1) * NV + k) * pery + oy + s) : 0.0;
+            } else {
+                fx0[s] = ld(fb + (long long)(0 * NV + k) * perx + ox + s);
+                fx1[s] = STAGE == 0 ? ld(fb + (long long)(1 * NV + k) * perx + ox + s) : 0.0;
+            }
+        }
+        if (STAGE == 0) {
+            double w = ld(Win + cell + (long long)k * g.plane);
+            double ws = w - (fx0[1] - fx0[0]) * inv_dx;
+            double wa = w - (fx1[1] - fx1[0]) * inv_dx;
+            if (DIM == 2) { ws = ws - (fy0[1] - fy0[0]) * inv_dy; wa = wa - (fy1[1] - fy1[0]) * inv_dy; }
+            out[k] = ws; acc[k] = wa;
+        } else {
+            double a = ld(Acc + cell + (long long)k * g.plane);
+            double wn = a - (fx0[1] - fx0[0]) * inv_dx;
+            if (DIM == 2) wn = wn - (fy0[1] - fy0[0]) * inv_dy;
+            out[k] = wn;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        Wout[cell + (long long)k * g.plane] = out[k];
+        if (STAGE == 0) Acc[cell + (long long)k * g.plane] = acc[k];
+    }
+    double ke = DIM == 2 ? 0.5 * (out[1] * out[1] + out[2] * out[2]) / out[0] : 0.5 * out[1] * out[1] / out[0];
+    double p = (P.gamma - 1.0) * (out[NV - 1] - ke);
+    if (!(out[0] > 0.0) || !(p > 0.0) || !isfinite(out[0]) || !isfinite(p)) ctrl->status = HGKS_ENONPHYSICAL;
+}
+
+inline unsigned int blocks_for(long long n, int tpb) { return (unsigned int)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------- host: timing helpers
+static cudaEvent_t take_event(hgks_solver* s)
+{
+    if (!s->event_pool.empty()) { cudaEvent_t e = s->event_pool.back(); s->event_pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename F>
+static void timed(hgks_solver* s, int cls, int nkernels, F&& launch)
+{
+    s->launches += nkernels;
+    if (!s->timing) { launch(); return; }
+    cudaEvent_t a = take_event(s), b = take_event(s);
+    cudaEventRecord(a, s->stream);
+    launch();
+    cudaEventRecord(b, s->stream);
+    s->timers.push_back(TimerRec{cls, a, b});
+}
+
+template <int DIM>
+static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
+{
+    const Params& P = s->P;
+    Sweep& S = s->sw[d];
+    cudaStream_t st = s->stream;
+    Ctrl* ctrl = s->ctrl;
+    constexpr int NV = DIM + 2;
+    int sms = device_sm_count();
+    timed(s, KC_RAWN, 1, [&] {
+        long long n = (long long)S.nlines * (S.nn + 4);
+        k_raw_nflags<NV><<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, Win, ctrl);
+    });
+    timed(s, KC_NORMAL, 1, [&] {
+        long long n = (long long)S.nlines * S.nm;
+        k_normal<NV><<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, Win, ctrl, stage);
+    });
+    timed(s, KC_NORMAL_AO, 1, [&] {
+        long long maxn = (long long)S.nlines * S.nm * 2;
+        unsigned int b = blocks_for(maxn, 128);
+        if (b > (unsigned)(sms * 8)) b = sms * 8;
+        k_normal_ao<NV><<<b, 128, 0, st>>>(P, S, Win, ctrl);
+    });
+    if constexpr (DIM == 2) {
+        timed(s, KC_RAWT, 1, [&] {
+            long long n = (long long)(S.nt + 2) * S.nm;
+            k_raw_tflags<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl);
+        });
+        timed(s, KC_TANG, 1, [&] {
+            long long n = (long long)S.nt * S.nm;
+            k_tang<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl, stage);
+        });
+        timed(s, KC_TANG_AO, 1, [&] {
+            long long maxn = (long long)S.nt * S.nm * 4;
+            unsigned int b = blocks_for(maxn, 128);
+            if (b > (unsigned)(sms * 8)) b = sms * 8;
+            k_tang_ao<<<b, 128, 0, st>>>(P, S, Win, ctrl);
+        });
+    }
+    if (s->capture) {
+        size_t nb = (size_t)S.nlines * (S.nn + 2);
+        cudaMemcpyAsync(s->cap[stage][d][0], S.flagN, nb, cudaMemcpyDeviceToDevice, st);
+        if (DIM == 2) cudaMemcpyAsync(s->cap[stage][d][1], S.flagT, (size_t)S.nt * S.nm, cudaMemcpyDeviceToDevice, st);
+    }
+    timed(s, KC_FLUX, 1, [&] {
+        long long n = (long long)S.nt * S.nm * (DIM == 2 ? 2 : 1);
+        if (stage == 0) k_flux<DIM, 0><<<blocks_for(n, 128), 128, 0, st>>>(P, S, ctrl);
+        else k_flux<DIM, 1><<<blocks_for(n, 128), 128, 0, st>>>(P, S, ctrl);
+    });
+}
+
+template <int DIM>
+static void enqueue_stage(hgks_solver* s, int stage)
+{
+    const Params& P = s->P;
+    cudaStream_t st = s->stream;
+    double* Win = stage == 0 ? s->W : s->Ws;
+    timed(s, KC_MISC, 1, [&] { k_begin_stage<<<1, 1, 0, st>>>(s->ctrl); });
+    timed(s, KC_GHOST, DIM == 2 ? 2 : 1, [&] {
+        int rowsI = DIM == 2 ? P.g.ny : 1;
+        k_ghost_x<<<blocks_for((long long)P.g.nv * rowsI * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
+        if (DIM == 2) k_ghost_y<<<blocks_for((long long)P.g.nv * (P.g.nx + 2 * NG) * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
+    });
+    enqueue_sweep<DIM>(s, 0, stage, Win);
+    if (DIM == 2) enqueue_sweep<DIM>(s, 1, stage, Win);
+    timed(s, KC_UPDATE, 1, [&] {
+        long long n = (long long)(DIM == 2 ? P.g.ny : 1) * P.g.nx;
+        if (stage == 0) k_update<DIM, 0><<<blocks_for(n, TPB), TPB, 0, st>>>(P, s->sw[0], s->sw[1], s->W, s->Ws, s->Acc, s->ctrl);
+        else k_update<DIM, 1><<<blocks_for(n, TPB), TPB, 0, st>>>(P, s->sw[0], s->sw[1], s->Ws, s->W, s->Acc, s->ctrl);
+    });
+}
+
+cudaError_t launch_step(hgks_solver* s, double t_end)
+{
+    const Params& P = s->P;
+    cudaStream_t st = s->stream;
+    double tol = 1e-12 * (fabs(t_end) > 1.0 ? fabs(t_end) : 1.0);
+    double h = P.g.dim == 2 ? (P.g.dx < P.g.dy ? P.g.dx : P.g.dy) : P.g.dx;
+    timed(s, KC_DT, P.fixed_dt > 0.0 ? 2 : 3, [&] {
+        k_begin_step<<<1, 1, 0, st>>>(s->ctrl);
+        if (!(P.fixed_dt > 0.0)) {
+            long long n = (long long)(P.g.dim == 2 ? P.g.ny : 1) * P.g.nx;
+            unsigned int b = blocks_for(n, TPB);
+            unsigned int cap = (unsigned)device_sm_count() * 4;
+            if (b > cap) b = cap;
+            k_dt<<<b, TPB, 0, st>>>(P, s->W, s->ctrl, h);
+        }
+        k_dt_final<<<1, 1, 0, st>>>(s->ctrl, P.cfl, P.fixed_dt, t_end, tol);
+    });
+    if (P.g.dim == 2) { enqueue_stage<2>(s, 0); enqueue_stage<2>(s, 1); }
+    else { enqueue_stage<1>(s, 0); enqueue_stage<1>(s, 1); }
+    timed(s, KC_MISC, 1, [&] { k_end_step<<<1, 1, 0, st>>>(s->ctrl); });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(hgks_solver* s, double t0)
+{
+    k_set_time<<<1, 1, 0, s->stream>>>(s->ctrl, t0);
+    return cudaGetLastError();
+}
+
+}  // namespace hgks

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Per step, from the identical input state: identical time step, bit-identical
+troubled flags of every pass (normal and tangential, both stages, both sweeps),
+and conservative state within 1e-11 relative (per component, relative to the
+component's largest magnitude).  At the final time of smooth runs: within 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_05572_gb300 import hgks, problems as P
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-11
+FINAL_TOL = 1e-9
+
+
+def rel_diff(a, b):
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    scale = np.abs(b).max(axis=1)
+    scale = np.maximum(scale, 1e-3 * scale.max())
+    return float(np.max(np.abs(a - b).max(axis=1) / scale))
+
+
+def gpu_step(cfg, W, t0=0.0):
+    s = hgks.Solver(cfg)
+    s.hgks_set_flag_capture(True)
+    s.hgks_set_state(np.ascontiguousarray(W), t0)
+    n = s.hgks_step(1e300, 1)
+    assert n == 1
+    out = s.hgks_get_state()
+    st = s.hgks_get_stats()
+    flags = {}
+    for stage in range(2):
+        for sweep in range(int(cfg["dim"])):
+            for kind in (0, 1) if int(cfg["dim"]) == 2 else (0,):
+                flags[(stage, sweep, "normal" if kind == 0 else "tang")] = s.hgks_get_flags(stage, sweep, kind)
+    s.hgks_destroy_solver()
+    return out, st, flags
+
+
+def check_step(cfg, W, label=""):
+    Wg, st, fg = gpu_step(cfg, W)
+    Wo, dt, fo = oracle.step_flags(cfg, W)
+    assert st["last_dt"] == dt, (label, st["last_dt"], dt)
+    assert set(fg) == set(fo)
+    for key in fo:
+        mism = int(np.count_nonzero(fg[key] != fo[key]))
+        assert mism == 0, (label, key, mism)
+    err = rel_diff(Wg, Wo)
+    assert err <= STEP_TOL, (label, err)
+    return Wo, st, fo, err
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2304_05572_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+# ------------------------------------------------------------------ 1D
+
+def test_sod_1d_steps_along_the_run():
+    cfg, W, t_end = P.sod_1d(200)
+    for n in range(6):
+        W, _, _, _ = check_step(cfg, W, "sod step %d" % n)
+    # march the oracle further and check steps near the end too
+    W2, t, _, _ = oracle.run(cfg, W, 0.15)
+    check_step(cfg, W2, "sod t=0.15")
+
+
+def test_sod_1d_full_run_close_to_oracle():
+    cfg, W, t_end = P.sod_1d(200)
+    Wg, tg, ng = hgks.run(cfg, W, t_end)
+    Wo, to, no, _ = oracle.run(cfg, W, t_end)
+    assert ng == no and tg == pytest.approx(to, abs=1e-15)
+    assert rel_diff(Wg, Wo) < 1e-9
+
+
+@pytest.mark.parametrize("mode", ["hybrid", "wenoao", "linear"])
+def test_sine_1d_final_time(mode):
+    cfg, W, t_end = P.sine_1d(40, recon_mode=mode)
+    Wg, tg, ng = hgks.run(cfg, W, t_end)
+    Wo, to, no, _ = oracle.run(cfg, W, t_end)
+    assert ng == no == 200
+    assert rel_diff(Wg, Wo) <= FINAL_TOL
+
+
+def test_blast_1d_positivity_path():
+    cfg, W, t_end = P.blast_1d(200)
+    W2, t, _, _ = oracle.run(cfg, W, 0.0262)      # just before the two blast waves collide
+    for n in range(3):
+        W2, _, _, _ = check_step(cfg, W2, "blast step %d" % n)
+
+
+# ------------------------------------------------------------------ 2D
+
+@pytest.mark.parametrize("nx,ny", [(37, 29), (64, 48)])
+def test_riemann4_steps(nx, ny):
+    cfg, W, _ = P.riemann4_2d(nx, ny=ny)
+    for n in range(3):
+        W, st, fo, err = check_step(cfg, W, "riemann step %d" % n)
+    assert sum(int(f.sum()) for f in fo.values()) > 0       # the troubled branch was exercised
+
+
+def test_riemann4_later_step():
+    cfg, W, _ = P.riemann4_2d(48)
+    W2, t, _, _ = oracle.run(cfg, W, 0.08)
+    check_step(cfg, W2, "riemann t=0.08")
+
+
+@pytest.mark.parametrize("mode", ["wenoao", "linear"])
+def test_recon_modes_2d(mode):
+    cfg, W, _ = P.random_smooth_2d(24, 20)
+    cfg["recon_mode"] = mode
+    check_step(cfg, W, mode)
+
+
+def test_paper_riemann_configurations():
+    for fn in (P.riemann_config1, P.riemann_config6):
+        cfg, W, _ = fn(40)
+        check_step(cfg, W, fn.__name__)
+
+
+def test_viscous_shock_tube_steps():
+    cfg, W, _ = P.viscous_shock_tube(48, 24, Re=200.0)
+    for n in range(2):
+        W, _, _, _ = check_step(cfg, W, "vst step %d" % n)
+
+
+def test_boundary_mix_and_tau_zero():
+    cfg, W, _ = P.random_smooth_2d(20, 17)
+    cfg["bc"] = ["periodic", "periodic", "reflect", "noslip"]
+    cfg["tau_zero"] = 1
+    check_step(cfg, W, "bc mix")
+    cfg["bc"] = ["extrap", "symmetry", "periodic", "periodic"]
+    cfg["tau_zero"] = 0
+    check_step(cfg, W, "bc mix 2")
+
+
+def test_vortex_final_time_smooth():
+    cfg, W, _ = P.vortex_2d(40)
+    Wg, tg, ng = hgks.run(cfg, W, 0.3)
+    Wo, to, no, _ = oracle.run(cfg, W, 0.3)
+    assert ng == no and tg == pytest.approx(to, abs=1e-14)
+    assert rel_diff(Wg, Wo) <= FINAL_TOL
+
+
+def test_sine_2d_final_time():
+    cfg, W, t_end = P.sine_2d(20)
+    Wg, tg, ng = hgks.run(cfg, W, t_end)
+    Wo, to, no, _ = oracle.run(cfg, W, t_end)
+    assert ng == no
+    assert rel_diff(Wg, Wo) <= FINAL_TOL
+
+
+def test_free_stream_bitwise_and_conservation():
+    cfg, W, _ = P.uniform_2d(33, ny=21)
+    Wg, _, n = hgks.run(cfg, W, 10.0, max_steps=3)
+    assert n == 3 and np.array_equal(Wg, W)
+    cfg, W, _ = P.riemann4_2d(40)
+    cfg["bc"] = ["periodic"] * 4
+    Wg, _, n = hgks.run(cfg, W, 10.0, max_steps=4)
+    assert np.all(np.abs(Wg.sum(axis=(1, 2)) - W.sum(axis=(1, 2))) <= 1e-13 * np.abs(W).sum() * n)
+
+
+# ------------------------------------------------------------------ full size (benchmark configuration)
+
+def test_riemann4_1024_full_size_step():
+    """One step of the 1024^2 benchmark configuration, whole grid against the oracle."""
+    cfg, W, _ = P.riemann4_2d(1024)
+    check_step(cfg, W, "1024^2")
+
+
+# ------------------------------------------------------------------ API behaviour
+
+def test_step_semantics_and_edge_cases():
+    import torch
+    cfg, W, _ = P.riemann4_2d(16)
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(W)
+    assert s.hgks_step(1.0, 0) == 0                     # max_steps = 0: nothing
+    np.testing.assert_array_equal(s.hgks_get_state(), W)
+    n = s.hgks_step(0.01, 1000)                         # stops at t_end, last step clipped
+    assert n > 0 and s.hgks_get_time() == pytest.approx(0.01, abs=1e-15)
+    assert s.hgks_step(0.01, 1000) == 0                 # already there
+    # device-pointer state in / out (torch only supplies the memory)
+    Wd = torch.from_numpy(W).cuda()
+    s.hgks_set_state(Wd)
+    out = torch.empty_like(Wd)
+    s.hgks_get_state(out)
+    assert torch.equal(out.cpu(), torch.from_numpy(W))
+    st = s.hgks_get_stats()
+    assert st["steps"] == 0 and st["t"] == 0.0
+    s.hgks_destroy_solver()
+
+
+def test_nonphysical_state_is_reported():
+    cfg, W, _ = P.riemann4_2d(16)
+    W = W.copy()
+    W[0, 5, 5] = -1.0
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(W)
+    with pytest.raises(hgks.HGKSError) as e:
+        s.hgks_step(1.0, 5)
+    assert e.value.code == hgks.HGKS_ENONPHYSICAL
+    assert s.hgks_get_stats()["status"] == hgks.HGKS_ENONPHYSICAL
+    s.hgks_destroy_solver()
+
+
+def test_troubled_counters():
+    cfg, W, _ = P.riemann4_2d(32)
+    s = hgks.Solver(cfg)
+    s.hgks_set_flag_capture(True)
+    s.hgks_set_state(W)
+    s.hgks_step(1e300, 1)
+    st = s.hgks_get_stats()
+    for stage in range(2):
+        for sweep in range(2):
+            fn = s.hgks_get_flags(stage, sweep, 0)[3:-3, 1:-1]       # interior lines and cells
+            ft = s.hgks_get_flags(stage, sweep, 1)
+            assert st["troubled"][stage, sweep, 0] == int(fn.sum())
+            assert st["examined"][stage, sweep, 0] == fn.size
+            assert st["troubled"][stage, sweep, 1] == sum(bin(int(v)).count("1") for v in ft.ravel())
+            assert st["examined"][stage, sweep, 1] == 4 * ft.size
+    s.hgks_destroy_solver()
