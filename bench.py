@@ -38,9 +38,14 @@ UNIT = "Mcell-stage/s"
 N_SIDE = 1024
 WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS, S2O4"
 
-# FP64 operations executed per Gauss-point flux evaluation of the 2D kernel with tau > 0
-# (DADD + DMUL + 2 x DFMA instructions per thread, ncu, 256^2 four-quadrant Riemann step).
-FLUX_FLOP_PER_GP_2D = None
+# FP64 operations per Gauss-point flux evaluation of the 2D kernel with tau > 0, counted by
+# ncu as DADD + DMUL + 2 x DFMA thread instructions per Gauss point (512^2 four-quadrant
+# Riemann step; identical per Gauss point at any grid size): first stage 1878, second 1802.
+FLUX_FLOP_PER_GP_2D = (1878 + 1802) / 2
+# DRAM bytes (read + write) per flux launch, ncu at 512^2 (111.0 MB first stage, 106.0 MB second),
+# scaled to 1024^2 by the Gauss points per launch (traffic is linear in them: Gauss-point
+# states in, per-Gauss-point fluxes out).
+FLUX_DRAM_BYTES_PER_GP = (111.0e6 + 106.0e6) / 2 / (2 * 512 * 513)
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 
@@ -258,7 +263,8 @@ def main():
         if FLUX_FLOP_PER_GP_2D:
             achieved = FLUX_FLOP_PER_GP_2D * gp_per_launch / (avg_ms * 1e-3) / 1e12
             roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                        "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                        "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
+                        "traffic": FLUX_DRAM_BYTES_PER_GP * gp_per_launch if n == N_SIDE else None,
                         "kernel": "gks_flux", "avg_launch_ms": avg_ms,
                         "peak_note": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (1.25 TFLOP/s nominal)"}
         else:

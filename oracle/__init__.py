@@ -79,7 +79,7 @@ def lib():
             L.or_run.argtypes = [ctypes.POINTER(Config), _DP, _DP, ctypes.c_double, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_int), _DP]
             L.or_step_flags.argtypes = [ctypes.POINTER(Config), _DP, ctypes.c_double, _DP,
-                                        ctypes.POINTER(_U8P)]
+                                        ctypes.POINTER(_U8P), ctypes.POINTER(_DP), _DP]
             L.or_cfl_dt.argtypes = [ctypes.POINTER(Config), _DP]
             L.or_cfl_dt.restype = ctypes.c_double
             L.or_moments.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -179,13 +179,17 @@ def flag_shapes(cfg: dict):
     return out
 
 
-def step_flags(cfg: dict, W: np.ndarray, dt: float = 0.0, threads: int = 0):
-    """One S2O4 step; returns (W_next, dt_used, flags) with flags[(stage, dir, kind)] arrays."""
+def step_flags(cfg: dict, W: np.ndarray, dt: float = 0.0, threads: int = 0, margins: bool = False,
+               wstar: np.ndarray = None):
+    """One S2O4 step; returns (W_next, dt_used, flags) with flags[(stage, dir, kind)] arrays,
+    and with margins=True also the relative decision margins in the same layout.  If wstar
+    (same shape as W) is given it receives the first-stage state W*."""
     c = make_config(cfg, threads)
     Wc = np.ascontiguousarray(W, dtype=np.float64).copy()
     shapes = flag_shapes(cfg)
-    bufs = {}
+    bufs, mbufs = {}, {}
     ptrs = (_U8P * 8)()
+    mptrs = (_DP * 8)()
     for s in range(2):
         for d in range(2):
             for ki, kind in enumerate(("normal", "tang")):
@@ -193,9 +197,16 @@ def step_flags(cfg: dict, W: np.ndarray, dt: float = 0.0, threads: int = 0):
                     a = np.zeros(shapes[(d, kind)], dtype=np.uint8)
                     bufs[(s, d, kind)] = a
                     ptrs[(s * 2 + d) * 2 + ki] = a.ctypes.data_as(_U8P)
+                    if margins:
+                        mb = np.full(shapes[(d, kind)], np.inf)
+                        mbufs[(s, d, kind)] = mb
+                        mptrs[(s * 2 + d) * 2 + ki] = mb.ctypes.data_as(_DP)
     dtu = ctypes.c_double(0.0)
-    st = lib().or_step_flags(ctypes.byref(c), _dp(Wc), float(dt), ctypes.byref(dtu), ptrs)
+    st = lib().or_step_flags(ctypes.byref(c), _dp(Wc), float(dt), ctypes.byref(dtu), ptrs,
+                             mptrs if margins else None, _dp(wstar) if wstar is not None else None)
     _check(st, "step")
+    if margins:
+        return Wc, dtu.value, bufs, mbufs
     return Wc, dtu.value, bufs
 
 

@@ -403,6 +403,39 @@ static int indicator_raw(const double* q, double Z1)
     return 1;
 }
 
+/* Robustness of the decision of indicator_raw under a perturbation of every input by
+ * eta = 1e-13 max|q|: the smallest ratio, over the steps taken, of the distance of a
+ * tested quantity from its threshold to the first-order change eta can cause in it
+ * (D: 20 eta; xbar = 1.7 N/D; xhat = -ahat1/(2 ahat2), whose change grows like
+ * 1/|ahat2|).  A ratio below 1 marks a decision that round-off can decide.  Test aid
+ * only; it does not change any decision. */
+static double indicator_margin(const double* q, double Z1)
+{
+    double scale = 0.0;
+    for (int s = 0; s < 5; s++) scale = fmax(scale, fabs(q[s]));
+    double eta = 1e-13 * scale + 1e-300;
+    double D = fma(-10.0, q[2], fma(4.0, q[0], q[1]) + fma(4.0, q[4], q[3]));
+    double r = fabs(fabs(D) - Z1) / (20.0 * eta);
+    if (fabs(D) <= Z1) return r;
+    double N = fma(2.0, q[0], q[1]) - fma(2.0, q[4], q[3]);
+    double a1 = -(N / 10.0);
+    double a2 = D / 34.0;
+    double xbar = -a1 / (2.0 * a2);
+    double dxbar = 1.7 * eta * (6.0 + 20.0 * fabs(N) / fabs(D)) / fabs(D);
+    r = fmin(r, fabs(fabs(xbar) - 2.5) / dxbar);
+    if (!(fabs(xbar) <= 2.5)) return r;
+    double ah1 = 0.5 * (q[3] - q[1]);
+    double ah2 = 0.5 * ((q[1] + q[3]) - 2.0 * q[2]);
+    if (fabs(ah2) <= 2.0 * eta) {
+        /* xhat = -ahat1/(2 ahat2) can take any value of magnitude >= (|ahat1| - eta)/(8 eta) */
+        double lo = (fabs(ah1) - eta) / (8.0 * eta);
+        return fmin(r, lo > fabs(xbar) + 0.25 ? (lo - fabs(xbar) - 0.25) / (fabs(xbar) + 0.25) : 0.0);
+    }
+    double xhat = -ah1 / (2.0 * ah2);
+    double dxhat = eta * (1.0 + 4.0 * fabs(xhat)) / (2.0 * fabs(ah2));
+    return fmin(r, fabs(fabs(xbar - xhat) - 0.25) / (dxhat + dxbar));
+}
+
 /* Step 5, Eqs. (26)-(27) (index typos corrected: Q_1 -> Q_{i+1}):
  * value and derivative at x_{i+1/2} from the window of cell i. */
 static void linear_left(const double* q, double inv12h, double* val, double* der)
@@ -774,7 +807,7 @@ static void fill_ghosts(const grid* g, double* Wp)
  *                                          passes of Q^l, Q^r, Q^l_n, Q^r_n at interface m,
  *                                          t in [0, nt), m in [0, nn]
  * where nn / nt are the cell counts normal / tangential to the sweep. */
-typedef struct { uint8_t* normal; uint8_t* tang; } flag_out;
+typedef struct { uint8_t* normal; uint8_t* tang; double* nmargin; double* tmargin; } flag_out;
 
 /* One sweep (dir 0: x-interfaces, dir 1: y-interfaces).  Writes, per interface
  * line segment, the line-averaged dt- and dt/2-integrated fluxes (global
@@ -811,16 +844,21 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
     for (int t = tlo; t < thi; t++) {
         int L = t - tlo;
         uint8_t raw[4096 + 8];
+        double rmar[4096 + 8];
         uint8_t* rawp = nn + 4 <= 4096 ? raw : (uint8_t*)malloc((size_t)nn + 8);
+        double* rmp = nn + 4 <= 4096 ? rmar : (double*)malloc(sizeof(double) * ((size_t)nn + 8));
         for (int n = -2; n <= nn + 1; n++) {
             int tr = 0;
+            double mg = INFINITY;
             if (mode == RECON_HYBRID)
                 for (int k = 0; k < nv; k++) {
                     double q[5];
                     for (int s = 0; s < 5; s++) q[s] = QL(k, t, n - 2 + s);
                     tr |= indicator_raw(q, Z1n);
+                    if (fo && fo->nmargin) mg = fmin(mg, indicator_margin(q, Z1n));
                 }
             rawp[n + 2] = (uint8_t)tr;
+            rmp[n + 2] = mg;
         }
         for (int n = -1; n <= nn; n++) {
             uint8_t f;
@@ -828,8 +866,11 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
             else if (mode == RECON_WENOAO) f = 1;
             else f = rawp[n + 1] | rawp[n + 2] | rawp[n + 3];        /* Step 4 */
             nflag[(size_t)L * (nn + 2) + (n + 1)] = f;
+            if (fo && fo->nmargin)
+                fo->nmargin[(size_t)L * (nn + 2) + (n + 1)] = fmin(rmp[n + 1], fmin(rmp[n + 2], rmp[n + 3]));
         }
         if (rawp != raw) free(rawp);
+        if (rmp != rmar) free(rmp);
         for (int m = 0; m < nm; m++) {
             double* out = line + ((size_t)L * nm + m) * 4 * nv;
             int il = m - 1, ir = m;                                   /* left cell, right cell */
@@ -868,6 +909,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
         for (int m = 0; m < nm; m++) {
             double gW[2][6][4];   /* per Gauss point: Wl, Wlx, Wly, Wr, Wrx, Wry (local order) */
             uint8_t tbits = 0;
+            double tmg = INFINITY;
             if (dim == 1) {
                 const double* ln = line + ((size_t)(t - tlo) * nm + m) * 4 * nv;
                 for (int k = 0; k < nv; k++) {
@@ -892,6 +934,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
                                     q[s] = line[((size_t)(tt - tlo) * nm + m) * 4 * nv + X * nv + k];
                                 }
                                 tr |= indicator_raw(q, Z1t);
+                                if (fo && fo->tmargin) tmg = fmin(tmg, indicator_margin(q, Z1t));
                             }
                         raw3[dt3 + 1] = tr;
                     }
@@ -945,6 +988,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
                         }
                 }
                 if (fo && fo->tang) fo->tang[(size_t)t * nm + m] = tbits;
+                if (fo && fo->tmargin) fo->tmargin[(size_t)t * nm + m] = tmg;
             }
             /* gas-kinetic flux at the Gauss points and the line average (weights 1/2) */
             int ngp = dim == 2 ? 2 : 1;
@@ -1017,6 +1061,8 @@ static int check_physical(const grid* g, const double* Wp)
 
 typedef struct {
     uint8_t* flags[2][2][2];   /* [stage][dir][0 normal, 1 tangential]; any may be NULL */
+    double* margins[2][2][2];  /* decision margins, same layout; any may be NULL */
+    double* wstar;             /* if not NULL: receives W* ([nv][ny][nx]) */
 } step_flags;
 
 /* One S2O4 step (Sec. 2.2): stage 1 with the dt and dt/2 fluxes at t_n gives
@@ -1047,7 +1093,8 @@ static int s2o4_step(const grid* g, double* Wp, double dt, step_flags* sf)
     /* ---- stage 1 ---- */
     fill_ghosts(g, Wn);
     for (int d = 0; d < ndir && st == OR_OK; d++) {
-        flag_out fo = {sf ? sf->flags[0][d][0] : NULL, sf ? sf->flags[0][d][1] : NULL};
+        flag_out fo = {sf ? sf->flags[0][d][0] : NULL, sf ? sf->flags[0][d][1] : NULL,
+                       sf ? sf->margins[0][d][0] : NULL, sf ? sf->margins[0][d][1] : NULL};
         st = sweep(g, Wn, d, dt, Fdt[d], Fh[d], &fo);
         for (size_t o = 0; o < nF[d]; o++) {
             Fn[d][o] = (4.0 * Fh[d][o] - Fdt[d][o]) / dt;                 /* Eq. (17) */
@@ -1070,11 +1117,17 @@ static int s2o4_step(const grid* g, double* Wp, double dt, step_flags* sf)
             }
     st = check_physical(g, Ws);
     if (st != OR_OK) goto done;
+    if (sf && sf->wstar)
+        for (int k = 0; k < nv; k++)
+            for (int j = 0; j < (dim == 2 ? ny : 1); j++)
+                for (int i = 0; i < nx; i++)
+                    sf->wstar[((size_t)k * (dim == 2 ? ny : 1) + j) * nx + i] = Ws[pidx(g, k, dim == 2 ? j : 0, i)];
 
     /* ---- stage 2 ---- */
     fill_ghosts(g, Ws);
     for (int d = 0; d < ndir && st == OR_OK; d++) {
-        flag_out fo = {sf ? sf->flags[1][d][0] : NULL, sf ? sf->flags[1][d][1] : NULL};
+        flag_out fo = {sf ? sf->flags[1][d][0] : NULL, sf ? sf->flags[1][d][1] : NULL,
+                       sf ? sf->margins[1][d][0] : NULL, sf ? sf->margins[1][d][1] : NULL};
         st = sweep(g, Ws, d, dt, Fdt[d], Fh[d], &fo);
         for (size_t o = 0; o < nF[d]; o++) {
             double dFs = 4.0 * (Fdt[d][o] - 2.0 * Fh[d][o]) / (dt * dt);    /* Eq. (18) at t* */
@@ -1171,8 +1224,9 @@ int or_run(const or_config* cfg, double* W, double* t, double t_end, int max_ste
 }
 
 /* One step with flag capture.  dt <= 0 selects the CFL time step.
- * flags: array of 8 pointers [stage][dir][normal/tangential], each may be NULL. */
-int or_step_flags(const or_config* cfg, double* W, double dt, double* dt_used, uint8_t** flags)
+ * flags, margins: arrays of 8 pointers [stage][dir][normal/tangential], each may be NULL. */
+int or_step_flags(const or_config* cfg, double* W, double dt, double* dt_used, uint8_t** flags, double** margins,
+                  double* wstar)
 {
     grid g;
     int st = grid_setup(cfg, &g);
@@ -1184,8 +1238,11 @@ int or_step_flags(const or_config* cfg, double* W, double dt, double* dt_used, u
     to_padded(&g, W, Wp);
     if (dt <= 0.0) dt = cfl_dt(&g, Wp);
     step_flags sf;
-    for (int s = 0; s < 2; s++) for (int d = 0; d < 2; d++) for (int k = 0; k < 2; k++)
+    for (int s = 0; s < 2; s++) for (int d = 0; d < 2; d++) for (int k = 0; k < 2; k++) {
         sf.flags[s][d][k] = flags ? flags[(s * 2 + d) * 2 + k] : NULL;
+        sf.margins[s][d][k] = margins ? margins[(s * 2 + d) * 2 + k] : NULL;
+    }
+    sf.wstar = wstar;
     st = s2o4_step(&g, Wp, dt, &sf);
     from_padded(&g, Wp, W);
     free(Wp);

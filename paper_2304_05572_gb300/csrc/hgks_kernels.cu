@@ -499,7 +499,10 @@ __global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
             Wq[2][k] = 0.0; Wq[5][k] = 0.0;
         }
     }
-    FluxConst fc{P.gamma, P.K, P.mu, P.c1, P.c2, P.viscous, P.tau_zero};
+    FluxConst fc;
+    fc.gamma = P.gamma; fc.gm1 = P.gamma - 1.0; fc.K = P.K;
+    fc.Kq = P.K + (double)DIM; fc.cslope = 4.0 / fc.Kq;
+    fc.mu = P.mu; fc.c1 = P.c1; fc.c2 = P.c2; fc.viscous = P.viscous; fc.tau_zero = P.tau_zero;
     double o0[NV], o1[NV];
     bool ok = gks_flux<DIM, STAGE>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1);
     if (!ok) { ctrl->status = HGKS_ENONPHYSICAL; return; }

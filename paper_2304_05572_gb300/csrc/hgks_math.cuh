@@ -17,6 +17,10 @@
 #pragma once
 
 #include <cstdint>
+#include <cmath>
+
+// flux arithmetic is also compiled for the host (unit checks of the formulas)
+#define HGKS_HD __host__ __device__
 
 namespace hgks {
 
@@ -320,243 +324,347 @@ __device__ __forceinline__ void gauss_ao(const ex* q, const AOConst& k, double* 
 }
 
 // ---------------------------------------------------------------- gas-kinetic flux
-// Normalised moments of a Maxwellian: u^n (full or one half line), v^m (full), xi^2, xi^4.
+// Normalised moments of a Maxwellian: u^n (full or one half line, n <= 6), v^m (full, m <= 5),
+// xi^2, xi^4.  Powers beyond these are never contracted.
 template <int DIM>
 struct Mom {
-    double u[8];
-    double v[DIM == 2 ? 7 : 1];
+    double u[7];
+    double v[DIM == 2 ? 6 : 1];
     double x2, x4;
 };
 
-// T(n, m) = <u^n v^m (a.psi)>; Tx = <u^n v^m xi^2 (a.psi)>
-template <int DIM, int N, int M>
-__device__ __forceinline__ double Tm(const double* a, const Mom<DIM>& m)
-{
-    if constexpr (DIM == 2) {
-        double um = m.u[N] * m.v[M];
-        double s = a[0] * um;
-        s = fma(a[1], m.u[N + 1] * m.v[M], s);
-        s = fma(a[2], m.u[N] * m.v[M + 1], s);
-        double e = fma(m.u[N + 2], m.v[M], fma(m.u[N], m.v[M + 2], um * m.x2));
-        return fma(0.5 * a[3], e, s);
-    } else {
-        double s = a[0] * m.u[N];
-        s = fma(a[1], m.u[N + 1], s);
-        double e = fma(m.u[N], m.x2, m.u[N + 2]);
-        return fma(0.5 * a[2], e, s);
-    }
-}
-template <int DIM, int N, int M>
-__device__ __forceinline__ double Tx(const double* a, const Mom<DIM>& m)
-{
-    if constexpr (DIM == 2) {
-        double um = m.u[N] * m.v[M];
-        double s = a[0] * um;
-        s = fma(a[1], m.u[N + 1] * m.v[M], s);
-        s = fma(a[2], m.u[N] * m.v[M + 1], s);
-        double e = fma(m.x2, fma(m.u[N + 2], m.v[M], m.u[N] * m.v[M + 2]), um * m.x4);
-        return fma(0.5 * a[3], e, s * m.x2);
-    } else {
-        double s = fma(a[1], m.u[N + 1], a[0] * m.u[N]);
-        double e = fma(m.x2, m.u[N + 2], m.u[N] * m.x4);
-        return fma(0.5 * a[2], e, s * m.x2);
-    }
-}
-// G(a; n, m) = <u^n v^m psi (a.psi)> (NV components)
-template <int DIM, int N, int M>
-__device__ __forceinline__ void Gm(const double* a, const Mom<DIM>& m, double* out)
-{
-    if constexpr (DIM == 2) {
-        out[0] = Tm<2, N, M>(a, m);
-        out[1] = Tm<2, N + 1, M>(a, m);
-        out[2] = Tm<2, N, M + 1>(a, m);
-        out[3] = 0.5 * (Tm<2, N + 2, M>(a, m) + Tm<2, N, M + 2>(a, m) + Tx<2, N, M>(a, m));
-    } else {
-        out[0] = Tm<1, N, 0>(a, m);
-        out[1] = Tm<1, N + 1, 0>(a, m);
-        out[2] = 0.5 * (Tm<1, N + 2, 0>(a, m) + Tx<1, N, 0>(a, m));
-    }
-}
-
-// Micro-slope a with <a> = b (b = dW / rho), closed form of the moment system of Eq. (8).
+// Primitive description of one Maxwellian (Eq. (3)): h = 1/(2 lambda) = p/rho.
 template <int DIM>
-__device__ __forceinline__ void slope_solve(const double* b, double U, double V, double lam, double K, double* a)
-{
-    if constexpr (DIM == 2) {
-        double q = fma(U, U, fma(V, V, (K + 2.0) / (2.0 * lam)));
-        double R4 = fma(-q, b[0], 2.0 * b[3]);
-        double R3 = fma(-V, b[0], b[2]);
-        double R2 = fma(-U, b[0], b[1]);
-        double a4 = (4.0 * lam * lam / (K + 2.0)) * fma(-2.0 * V, R3, fma(-2.0 * U, R2, R4));
-        double a3 = fma(-V, a4, 2.0 * lam * R3);
-        double a2 = fma(-U, a4, 2.0 * lam * R2);
-        a[3] = a4; a[2] = a3; a[1] = a2;
-        a[0] = fma(-0.5 * a4, q, fma(-V, a3, fma(-U, a2, b[0])));
-    } else {
-        double q = fma(U, U, (K + 1.0) / (2.0 * lam));
-        double R3 = fma(-q, b[0], 2.0 * b[2]);
-        double R2 = fma(-U, b[0], b[1]);
-        double a3 = (4.0 * lam * lam / (K + 1.0)) * fma(-2.0 * U, R2, R3);
-        double a2 = fma(-U, a3, 2.0 * lam * R2);
-        a[2] = a3; a[1] = a2;
-        a[0] = fma(-0.5 * a3, q, fma(-U, a2, b[0]));
-    }
-}
+struct MState {
+    double rho, ri, U, V, p, h, lam, E;
+    double q, lam2c, two_lam;      // slope-solve constants: q = |U|^2 + Kq h, lam2c = lam^2 4/Kq
+};
 
 struct FluxConst {
-    double gamma, K, mu, c1, c2;
+    double gamma, gm1, K, Kq, cslope, mu, c1, c2;   // Kq = K + D (D = 2 in 2D, 1 in 1D), cslope = 4/Kq
     int viscous, tau_zero;
 };
 
-// Primitive state; returns false if rho <= 0 or p <= 0.
 template <int DIM>
-__device__ __forceinline__ bool prim(const double* W, double gam, double& rho, double& U, double& V, double& lam, double& p)
+HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MState<DIM>& s)
 {
-    rho = W[0];
-    double ri = 1.0 / rho;
-    U = W[1] * ri;
-    V = DIM == 2 ? W[2] * ri : 0.0;
-    double ke = DIM == 2 ? fma(U, W[1], V * W[2]) : U * W[1];
-    p = (gam - 1.0) * fma(-0.5, ke, W[DIM + 1]);
-    lam = 0.5 * rho / p;
-    return rho > 0.0 && p > 0.0;
+    s.rho = W[0];
+    s.ri = 1.0 / s.rho;
+    s.U = W[1] * s.ri;
+    s.V = DIM == 2 ? W[2] * s.ri : 0.0;
+    s.E = W[DIM + 1];
+    double mu2 = DIM == 2 ? fma(W[1], s.U, W[2] * s.V) : W[1] * s.U;
+    s.p = fc.gm1 * fma(-0.5, mu2, s.E);
+    s.h = s.p * s.ri;
+    s.lam = 0.5 / s.h;
+    s.q = fma(s.U, s.U, fma(s.V, s.V, fc.Kq * s.h));
+    s.lam2c = s.lam * s.lam * fc.cslope;
+    s.two_lam = 2.0 * s.lam;
+    return s.rho > 0.0 && s.p > 0.0;
+}
+
+// Micro-slope a with <a> = b (b = dW/rho): closed-form inverse of the moment system of Eq. (8).
+template <int DIM>
+HGKS_HD __forceinline__ void slope_solve(const double* b, const MState<DIM>& s, double* a)
+{
+    if constexpr (DIM == 2) {
+        double R4 = fma(-s.q, b[0], 2.0 * b[3]);
+        double R3 = fma(-s.V, b[0], b[2]);
+        double R2 = fma(-s.U, b[0], b[1]);
+        double a4 = s.lam2c * fma(-2.0 * s.V, R3, fma(-2.0 * s.U, R2, R4));
+        double a3 = fma(-s.V, a4, s.two_lam * R3);
+        double a2 = fma(-s.U, a4, s.two_lam * R2);
+        a[3] = a4; a[2] = a3; a[1] = a2;
+        a[0] = fma(-0.5 * s.q, a4, fma(-s.V, a3, fma(-s.U, a2, b[0])));
+    } else {
+        double R3 = fma(-s.q, b[0], 2.0 * b[2]);
+        double R2 = fma(-s.U, b[0], b[1]);
+        double a3 = s.lam2c * fma(-2.0 * s.U, R2, R3);
+        double a2 = fma(-s.U, a3, s.two_lam * R2);
+        a[2] = a3; a[1] = a2;
+        a[0] = fma(-0.5 * s.q, a3, fma(-s.U, a2, b[0]));
+    }
+}
+
+// Euler flux Jacobians applied to a direction: dF/dW d (x) and dG/dW d (y).
+// For a Maxwellian g and a slope a with <a> = d, int u psi (a.psi) g = dF/dW d, so these
+// give the moments int psi (a1 u + a2 v) g of the compatibility condition (Eq. (9)) and the
+// flux moment of the equilibrium time slope in closed form.
+template <int DIM>
+HGKS_HD __forceinline__ void jac_x(const MState<DIM>& s, const double* d, const double gm1, double* out)
+{
+    const double g = s.E + s.p;     // rho H
+    if constexpr (DIM == 2) {
+        const double hq = 0.5 * fma(s.U, s.U, s.V * s.V);
+        const double dp = gm1 * fma(hq, d[0], fma(-s.U, d[1], fma(-s.V, d[2], d[3])));
+        const double dU = (d[1] - s.U * d[0]) * s.ri;
+        out[0] = d[1];
+        out[1] = fma(s.U, fma(-s.U, d[0], 2.0 * d[1]), dp);
+        out[2] = fma(s.V, d[1], s.U * fma(-s.V, d[0], d[2]));
+        out[3] = fma(dU, g, s.U * (d[3] + dp));
+    } else {
+        const double hq = 0.5 * s.U * s.U;
+        const double dp = gm1 * fma(hq, d[0], fma(-s.U, d[1], d[2]));
+        const double dU = (d[1] - s.U * d[0]) * s.ri;
+        out[0] = d[1];
+        out[1] = fma(s.U, fma(-s.U, d[0], 2.0 * d[1]), dp);
+        out[2] = fma(dU, g, s.U * (d[2] + dp));
+    }
+}
+
+HGKS_HD __forceinline__ void jac_y(const MState<2>& s, const double* e, const double gm1, double* out)
+{
+    const double g = s.E + s.p;
+    const double hq = 0.5 * fma(s.U, s.U, s.V * s.V);
+    const double dp = gm1 * fma(hq, e[0], fma(-s.U, e[1], fma(-s.V, e[2], e[3])));
+    const double dV = (e[2] - s.V * e[0]) * s.ri;
+    out[0] = e[2];
+    out[1] = fma(s.U, e[2], s.V * fma(-s.U, e[0], e[1]));
+    out[2] = fma(s.V, fma(-s.V, e[0], 2.0 * e[2]), dp);
+    out[3] = fma(dV, g, s.V * (e[3] + dp));
+}
+
+// Time derivative of the conserved variables for the slopes d (x) and e (y) from the Euler
+// compatibility (Eq. (9)): W_t = -(dF/dW d + dG/dW e).
+template <int DIM>
+HGKS_HD __forceinline__ void w_t(const MState<DIM>& s, const double* d, const double* e, const double gm1, double* out)
+{
+    jac_x<DIM>(s, d, gm1, out);
+    if constexpr (DIM == 2) {
+        double t[4];
+        jac_y(s, e, gm1, t);
+#pragma unroll
+        for (int k = 0; k < 4; k++) out[k] = -(out[k] + t[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) out[k] = -out[k];
+    }
+}
+
+// Directional derivatives of Pi(W) = int u^2 psi g and Sigma(W) = int u v psi g (g the Maxwellian
+// of W) along d (and e).  Since <abar> = d makes (abar.psi) g0 the derivative of g0 along d,
+// int u psi (abar1 u + abar2 v) g0 = Pi'(W) d + Sigma'(W) e: the (abar1 u + abar2 v) g0 flux
+// moment of Eq. (10) without solving for abar.  With h = p/rho and chain rule through (rho, U, V, h).
+template <int DIM>
+HGKS_HD __forceinline__ void pi_sigma_dir(const MState<DIM>& s, const double* d, const double* e, const double gm1,
+                                          const double K, double* out)
+{
+    const double U = s.U, V = s.V, h = s.h, r = s.rho;
+    const double U2 = U * U;
+    if constexpr (DIM == 2) {
+        const double V2 = V * V;
+        const double hq = 0.5 * (U2 + V2);
+        // Pi along d
+        double dU = (d[1] - U * d[0]) * s.ri, dV = (d[2] - V * d[0]) * s.ri;
+        double dp = gm1 * fma(hq, d[0], fma(-U, d[1], fma(-V, d[2], d[3])));
+        double dh = (dp - h * d[0]) * s.ri;
+        const double u2 = U2 + h, v2 = V2 + h;
+        const double p0 = u2, p1 = U * (U2 + 3.0 * h), p2 = u2 * V;
+        const double p3 = 0.5 * (fma(U2, U2 + 6.0 * h, 3.0 * h * h) + u2 * v2 + u2 * K * h);
+        const double p3U = U * (2.0 * U2 + 6.0 * h + v2 + K * h);
+        const double p3h = 0.5 * (7.0 * U2 + V2 + 8.0 * h + K * (U2 + 2.0 * h));
+        out[0] = fma(p0, d[0], r * fma(2.0 * U, dU, dh));
+        out[1] = fma(p1, d[0], r * fma(3.0 * u2, dU, 3.0 * U * dh));
+        out[2] = fma(p2, d[0], r * fma(2.0 * U * V, dU, fma(u2, dV, V * dh)));
+        out[3] = fma(p3, d[0], r * fma(p3U, dU, fma(u2 * V, dV, p3h * dh)));
+        // Sigma along e
+        dU = (e[1] - U * e[0]) * s.ri; dV = (e[2] - V * e[0]) * s.ri;
+        dp = gm1 * fma(hq, e[0], fma(-U, e[1], fma(-V, e[2], e[3])));
+        dh = (dp - h * e[0]) * s.ri;
+        const double UV = U * V, k6 = 6.0 + K;
+        const double s0 = UV, s1 = u2 * V, s2 = U * v2, s3 = 0.5 * UV * (U2 + V2 + k6 * h);
+        const double s3U = 0.5 * V * (3.0 * U2 + V2 + k6 * h);
+        const double s3V = 0.5 * U * (U2 + 3.0 * V2 + k6 * h);
+        const double s3h = 0.5 * k6 * UV;
+        out[0] += fma(s0, e[0], r * fma(V, dU, U * dV));
+        out[1] += fma(s1, e[0], r * fma(2.0 * UV, dU, fma(u2, dV, V * dh)));
+        out[2] += fma(s2, e[0], r * fma(v2, dU, fma(2.0 * UV, dV, U * dh)));
+        out[3] += fma(s3, e[0], r * fma(s3U, dU, fma(s3V, dV, s3h * dh)));
+    } else {
+        (void)e;
+        const double hq = 0.5 * U2;
+        const double dU = (d[1] - U * d[0]) * s.ri;
+        const double dp = gm1 * fma(hq, d[0], fma(-U, d[1], d[2]));
+        const double dh = (dp - h * d[0]) * s.ri;
+        const double u2 = U2 + h;
+        const double p0 = u2, p1 = U * (U2 + 3.0 * h);
+        const double p2 = 0.5 * (fma(U2, U2 + 6.0 * h, 3.0 * h * h) + u2 * K * h);
+        const double p2U = U * (2.0 * U2 + 6.0 * h + K * h);
+        const double p2h = 0.5 * (6.0 * U2 + 6.0 * h + K * (U2 + 2.0 * h));
+        out[0] = fma(p0, d[0], r * fma(2.0 * U, dU, dh));
+        out[1] = fma(p1, d[0], r * fma(3.0 * u2, dU, 3.0 * U * dh));
+        out[2] = fma(p2, d[0], r * fma(p2U, dU, p2h * dh));
+    }
+}
+
+// T(n, m) = <u^n v^m (a.psi)>, Tx(n, m) = <u^n v^m xi^2 (a.psi)>, G = <u^n v^m psi (a.psi)>.
+template <int DIM, int N, int M>
+HGKS_HD __forceinline__ void Gm(const double* a, const Mom<DIM>& m, double* out)
+{
+    if constexpr (DIM == 2) {
+        const double ha3 = 0.5 * a[3];
+        // Au(n) = a0 u_n + a1 u_{n+1} + a3/2 u_{n+2};  Bv(k) = a2 v_{k+1} + a3/2 (v_{k+2} + x2 v_k)
+        const double Au0 = fma(a[1], m.u[N + 1], fma(ha3, m.u[N + 2], a[0] * m.u[N]));
+        const double Au1 = fma(a[1], m.u[N + 2], fma(ha3, m.u[N + 3], a[0] * m.u[N + 1]));
+        const double Au2 = fma(a[1], m.u[N + 3], fma(ha3, m.u[N + 4], a[0] * m.u[N + 2]));
+        const double Bv0 = fma(a[2], m.v[M + 1], ha3 * fma(m.x2, m.v[M], m.v[M + 2]));
+        const double Bv1 = fma(a[2], m.v[M + 2], ha3 * fma(m.x2, m.v[M + 1], m.v[M + 3]));
+        const double Bv2 = fma(a[2], m.v[M + 3], ha3 * fma(m.x2, m.v[M + 2], m.v[M + 4]));
+        out[0] = fma(m.v[M], Au0, m.u[N] * Bv0);                        // T(n, m)
+        out[1] = fma(m.v[M], Au1, m.u[N + 1] * Bv0);                    // T(n+1, m)
+        out[2] = fma(m.v[M + 1], Au0, m.u[N] * Bv1);                    // T(n, m+1)
+        const double Tn2 = fma(m.v[M], Au2, m.u[N + 2] * Bv0);          // T(n+2, m)
+        const double Tm2 = fma(m.v[M + 2], Au0, m.u[N] * Bv2);          // T(n, m+2)
+        const double Tx = fma(m.x2, fma(m.v[M], Au0, m.u[N] * fma(a[2], m.v[M + 1], ha3 * m.v[M + 2])),
+                              ha3 * m.x4 * (m.u[N] * m.v[M]));           // Tx(n, m)
+        out[3] = 0.5 * (Tn2 + Tm2 + Tx);
+    } else {
+        const double ha2 = 0.5 * a[2];
+        // T(n) = a0 u_n + a1 u_{n+1} + a2/2 (u_{n+2} + x2 u_n)
+        const double c0 = fma(ha2, m.x2, a[0]);
+        const double T0 = fma(a[1], m.u[N + 1], fma(ha2, m.u[N + 2], c0 * m.u[N]));
+        const double T1 = fma(a[1], m.u[N + 2], fma(ha2, m.u[N + 3], c0 * m.u[N + 1]));
+        const double T2 = fma(a[1], m.u[N + 3], fma(ha2, m.u[N + 4], c0 * m.u[N + 2]));
+        const double Tx = fma(m.x2, fma(a[1], m.u[N + 1], fma(ha2, m.u[N + 2], a[0] * m.u[N])), ha2 * m.x4 * m.u[N]);
+        out[0] = T0; out[1] = T1; out[2] = 0.5 * (T2 + Tx);
+    }
 }
 
 template <int DIM>
-__device__ __forceinline__ void full_moments(double U, double V, double lam, double K, Mom<DIM>& m)
+HGKS_HD __forceinline__ void fill_vx(const MState<DIM>& s, const FluxConst& fc, Mom<DIM>& m)
 {
-    double h = 0.5 / lam;
-    m.u[0] = 1.0; m.u[1] = U;
-#pragma unroll
-    for (int n = 0; n < 6; n++) m.u[n + 2] = fma(U, m.u[n + 1], (n + 1) * h * m.u[n]);
     if constexpr (DIM == 2) {
-        m.v[0] = 1.0; m.v[1] = V;
-#pragma unroll
-        for (int n = 0; n < 5; n++) m.v[n + 2] = fma(V, m.v[n + 1], (n + 1) * h * m.v[n]);
+        m.v[0] = 1.0;
+        m.v[1] = s.V;
+        m.v[2] = fma(s.V, m.v[1], s.h);
+        m.v[3] = fma(s.V, m.v[2], 2.0 * s.h * m.v[1]);
+        m.v[4] = fma(s.V, m.v[3], 3.0 * s.h * m.v[2]);
+        m.v[5] = fma(s.V, m.v[4], 4.0 * s.h * m.v[3]);
     } else {
         m.v[0] = 1.0;
     }
-    m.x2 = K * h;
-    m.x4 = m.x2 * (K + 2.0) * h;
+    m.x2 = fc.K * s.h;
+    m.x4 = m.x2 * (fc.K + 2.0) * s.h;
 }
 
-// Half-line moments: sign > 0 for u > 0 (left state), < 0 for u < 0 (right state).
+// <u^(n+2)> = U <u^(n+1)> + (n+1) h <u^n>, on the full line or either half line.
 template <int DIM>
-__device__ __forceinline__ void half_moments(double U, double V, double lam, double K, int sign, Mom<DIM>& m)
+HGKS_HD __forceinline__ void recur_u(const MState<DIM>& s, Mom<DIM>& m)
 {
-    double h = 0.5 / lam;
-    double sl = sqrt(lam);
-    double x = sl * U;
-    double e = 0.5 * exp(-x * x) * (0.56418958354775628695 / sl);   // exp(-lam U^2) / (2 sqrt(pi lam))
-    if (sign > 0) { m.u[0] = 0.5 * erfc(-x); m.u[1] = fma(U, m.u[0], e); }
-    else          { m.u[0] = 0.5 * erfc(x);  m.u[1] = fma(U, m.u[0], -e); }
 #pragma unroll
-    for (int n = 0; n < 6; n++) m.u[n + 2] = fma(U, m.u[n + 1], (n + 1) * h * m.u[n]);
-    if constexpr (DIM == 2) {
-        m.v[0] = 1.0; m.v[1] = V;
-#pragma unroll
-        for (int n = 0; n < 5; n++) m.v[n + 2] = fma(V, m.v[n + 1], (n + 1) * h * m.v[n]);
-    } else {
-        m.v[0] = 1.0;
-    }
-    m.x2 = K * h;
-    m.x4 = m.x2 * (K + 2.0) * h;
+    for (int n = 0; n < 5; n++) m.u[n + 2] = fma(s.U, m.u[n + 1], ((double)(n + 1) * s.h) * m.u[n]);
 }
 
-// Gas-kinetic flux at one Gauss point in the local frame (x = normal).
-// Inputs: side states and their normal (x) and tangential (y, 2D) derivatives.
-// Outputs for the S2O4 stages, with Fd = F(dt), Fh = F(dt/2) of Eq. (12):
-//   STAGE 0: o0 = Fh (for W*, Eq. (19)), o1 = (8 Fh - Fd)/3 = dt F^n + dt^2/6 dF^n (Eqs. (17),(18),(20))
+template <int DIM>
+HGKS_HD __forceinline__ void full_moments(const MState<DIM>& s, const FluxConst& fc, Mom<DIM>& m)
+{
+    m.u[0] = 1.0;
+    m.u[1] = s.U;
+    recur_u<DIM>(s, m);
+    fill_vx<DIM>(s, fc, m);
+}
+
+// Half-line moments of the left state over u > 0 (sign = +1) or of the right state over
+// u < 0 (sign = -1): <1> = erfc(-+sqrt(lam) U)/2, <u> = U <1> +- exp(-lam U^2)/(2 sqrt(pi lam)).
+template <int DIM>
+HGKS_HD __forceinline__ void half_moments(const MState<DIM>& s, int sign, const FluxConst& fc, Mom<DIM>& m)
+{
+    const double sl = sqrt(s.lam);
+    const double x = sl * s.U;
+    const double e = exp(-x * x) * (0.56418958354775628695 * s.h * sl);   // 1/sqrt(pi) h sqrt(lam)
+    m.u[0] = 0.5 * erfc(sign > 0 ? -x : x);
+    m.u[1] = fma(s.U, m.u[0], sign > 0 ? e : -e);
+    recur_u<DIM>(s, m);
+    fill_vx<DIM>(s, fc, m);
+}
+
+// <psi> and <u psi> of one (half-line) Maxwellian, normalised.
+template <int DIM>
+HGKS_HD __forceinline__ void psi_mom(const Mom<DIM>& m, double* out0, double* out1)
+{
+    if constexpr (DIM == 2) {
+        const double w = m.v[2] + m.x2;
+        out0[0] = m.u[0]; out0[1] = m.u[1]; out0[2] = m.u[0] * m.v[1]; out0[3] = 0.5 * fma(m.u[0], w, m.u[2]);
+        out1[0] = m.u[1]; out1[1] = m.u[2]; out1[2] = m.u[1] * m.v[1]; out1[3] = 0.5 * fma(m.u[1], w, m.u[3]);
+    } else {
+        out0[0] = m.u[0]; out0[1] = m.u[1]; out0[2] = 0.5 * fma(m.u[0], m.x2, m.u[2]);
+        out1[0] = m.u[1]; out1[1] = m.u[2]; out1[2] = 0.5 * fma(m.u[1], m.x2, m.u[3]);
+    }
+}
+
+// Gas-kinetic flux at one Gauss point in the local frame (x = normal); Sec. 2.1, Eqs. (6)-(12),
+// (46)-(47), collision time of Sec. 3.  Inputs: side states and their normal (x) and tangential
+// (y, 2D) derivatives.  With Fd = F(dt), Fh = F(dt/2) of Eq. (12):
+//   STAGE 0: o0 = Fh (for W*, Eq. (19)),  o1 = (8 Fh - Fd)/3 = dt F^n + dt^2/6 dF^n (Eqs. (17)-(18), (20))
 //   STAGE 1: o0 = (4/3)(Fd - 2 Fh) = dt^2/3 dF* (Eqs. (18), (20))
 // Returns false if a side or the equilibrium state is non-physical.
 template <int DIM, int STAGE>
-__device__ __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, const double* Wlx, const double* Wly,
+HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, const double* Wlx, const double* Wly,
                                          const double* Wr, const double* Wrx, const double* Wry, double dt,
                                          double* o0, double* o1)
 {
     constexpr int NV = DIM + 2;
-    const double K = fc.K;
-    double rl, Ul, Vl, ll, pl, rr, Ur, Vr, lr, pr;
-    bool ok = prim<DIM>(Wl, fc.gamma, rl, Ul, Vl, ll, pl);
-    ok = prim<DIM>(Wr, fc.gamma, rr, Ur, Vr, lr, pr) && ok;
-    if (!ok) return false;
+    MState<DIM> sl, sr;
+    bool okl = make_state<DIM>(Wl, fc, sl);
+    bool okr = make_state<DIM>(Wr, fc, sr);
+    if (!(okl && okr)) return false;
     Mom<DIM> ml, mr;
-    half_moments<DIM>(Ul, Vl, ll, K, +1, ml);
-    half_moments<DIM>(Ur, Vr, lr, K, -1, mr);
-    const double ril = 1.0 / rl, rir = 1.0 / rr;
+    half_moments<DIM>(sl, +1, fc, ml);
+    half_moments<DIM>(sr, -1, fc, mr);
 
-    // micro-slopes of each side (Eq. (8)): b = dW / rho
+    // micro-slopes of each side, Eq. (8)
     double a1l[NV], a1r[NV], a2l[NV], a2r[NV], b[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) b[k] = Wlx[k] * ril;
-    slope_solve<DIM>(b, Ul, Vl, ll, K, a1l);
+    for (int k = 0; k < NV; k++) b[k] = Wlx[k] * sl.ri;
+    slope_solve<DIM>(b, sl, a1l);
 #pragma unroll
-    for (int k = 0; k < NV; k++) b[k] = Wrx[k] * rir;
-    slope_solve<DIM>(b, Ur, Vr, lr, K, a1r);
+    for (int k = 0; k < NV; k++) b[k] = Wrx[k] * sr.ri;
+    slope_solve<DIM>(b, sr, a1r);
     if constexpr (DIM == 2) {
 #pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = Wly[k] * ril;
-        slope_solve<DIM>(b, Ul, Vl, ll, K, a2l);
+        for (int k = 0; k < NV; k++) b[k] = Wly[k] * sl.ri;
+        slope_solve<DIM>(b, sl, a2l);
 #pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = Wry[k] * rir;
-        slope_solve<DIM>(b, Ur, Vr, lr, K, a2r);
+        for (int k = 0; k < NV; k++) b[k] = Wry[k] * sr.ri;
+        slope_solve<DIM>(b, sr, a2r);
     }
 
-    // equilibrium state and slopes by kinetic weighting, Eqs. (46)-(47)
-    double Wc[NV], Wcx[NV], Wcy[NV], t1[NV], t2[NV];
-    {
-        double one[NV];
+    // equilibrium state and its slopes by kinetic weighting, Eqs. (46)-(47)
+    double Wc[NV], Wcx[NV], Wcy[NV], pl0[NV], pl1[NV], pr0[NV], pr1[NV], t1[NV], t2[NV];
+    psi_mom<DIM>(ml, pl0, pl1);
+    psi_mom<DIM>(mr, pr0, pr1);
 #pragma unroll
-        for (int k = 0; k < NV; k++) one[k] = k == 0 ? 1.0 : 0.0;
-        Gm<DIM, 0, 0>(one, ml, t1);
-        Gm<DIM, 0, 0>(one, mr, t2);
+    for (int k = 0; k < NV; k++) Wc[k] = fma(sl.rho, pl0[k], sr.rho * pr0[k]);
+    Gm<DIM, 0, 0>(a1l, ml, t1);
+    Gm<DIM, 0, 0>(a1r, mr, t2);
 #pragma unroll
-        for (int k = 0; k < NV; k++) Wc[k] = fma(rl, t1[k], rr * t2[k]);
-        Gm<DIM, 0, 0>(a1l, ml, t1);
-        Gm<DIM, 0, 0>(a1r, mr, t2);
-#pragma unroll
-        for (int k = 0; k < NV; k++) Wcx[k] = fma(rl, t1[k], rr * t2[k]);
-        if constexpr (DIM == 2) {
-            Gm<DIM, 0, 0>(a2l, ml, t1);
-            Gm<DIM, 0, 0>(a2r, mr, t2);
-#pragma unroll
-            for (int k = 0; k < NV; k++) Wcy[k] = fma(rl, t1[k], rr * t2[k]);
-        }
-    }
-    double rc, Uc, Vc, lc, pc;
-    if (!prim<DIM>(Wc, fc.gamma, rc, Uc, Vc, lc, pc)) return false;
-    Mom<DIM> mc;
-    full_moments<DIM>(Uc, Vc, lc, K, mc);
-    const double ric = 1.0 / rc;
-    double ab1[NV], ab2[NV], Ab[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) b[k] = Wcx[k] * ric;
-    slope_solve<DIM>(b, Uc, Vc, lc, K, ab1);
+    for (int k = 0; k < NV; k++) Wcx[k] = fma(sl.rho, t1[k], sr.rho * t2[k]);
     if constexpr (DIM == 2) {
+        Gm<DIM, 0, 0>(a2l, ml, t1);
+        Gm<DIM, 0, 0>(a2r, mr, t2);
 #pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = Wcy[k] * ric;
-        slope_solve<DIM>(b, Uc, Vc, lc, K, ab2);
+        for (int k = 0; k < NV; k++) Wcy[k] = fma(sl.rho, t1[k], sr.rho * t2[k]);
     }
-    // compatibility for the equilibrium time slope (Eq. (9))
-    Gm<DIM, 1, 0>(ab1, mc, t1);
-    if constexpr (DIM == 2) {
-        Gm<DIM, 0, 1>(ab2, mc, t2);
-#pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = -(t1[k] + t2[k]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = -t1[k];
-    }
-    slope_solve<DIM>(b, Uc, Vc, lc, K, Ab);
+    MState<DIM> sc;
+    if (!make_state<DIM>(Wc, fc, sc)) return false;
+
+    // equilibrium flux moments: M1 = int u psi g0 = F(Wc);  M3 = int u psi Abar g0 = dF/dW Wc_t
+    double M1[NV], M3[NV], Wct[NV];
+    M1[0] = Wc[1];
+    M1[1] = fma(Wc[1], sc.U, sc.p);
+    if constexpr (DIM == 2) M1[2] = Wc[1] * sc.V;
+    M1[NV - 1] = sc.U * (sc.E + sc.p);
+    w_t<DIM>(sc, Wcx, Wcy, fc.gm1, Wct);
+    jac_x<DIM>(sc, Wct, fc.gm1, M3);
 
     // collision time (Sec. 3 preamble)
-    const double jump = fabs((pl - pr) / (pl + pr));
+    const double jump = fabs((sl.p - sr.p) / (sl.p + sr.p));
     double tau;
     if (fc.tau_zero) tau = 0.0;
-    else if (fc.viscous) tau = fma(fc.c2 * jump, dt, fc.mu / pc);
+    else if (fc.viscous) tau = fma(fc.c2 * jump, dt, fc.mu / sc.p);
     else tau = (fc.c1 + fc.c2 * jump) * dt;
 
-    // time coefficients of Eq. (10) integrated over [0, d], for d = dt and dt/2
+    // time integrals of the factors of Eq. (10) over [0, d], d = dt and dt/2
     double Cd[6], Ch[6];
     if (tau == 0.0) {
         Cd[0] = dt; Cd[1] = 0.0; Cd[2] = 0.5 * dt * dt; Cd[3] = 0.0; Cd[4] = 0.0; Cd[5] = 0.0;
@@ -566,11 +674,11 @@ __device__ __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, 
         const double ed = eh * eh;
         const double tt = tau * tau;
 #pragma unroll
-        for (int s = 0; s < 2; s++) {
-            const double d = s == 0 ? dt : 0.5 * dt;
-            const double e = s == 0 ? ed : eh;
+        for (int s2 = 0; s2 < 2; s2++) {
+            const double d = s2 == 0 ? dt : 0.5 * dt;
+            const double e = s2 == 0 ? ed : eh;
             const double om = 1.0 - e;
-            double* C = s == 0 ? Cd : Ch;
+            double* C = s2 == 0 ? Cd : Ch;
             C[0] = fma(-tau, om, d);
             C[1] = fma(2.0 * tt, om, -tau * d * (1.0 + e));
             C[2] = fma(tt, om, d * fma(0.5, d, -tau));
@@ -579,7 +687,6 @@ __device__ __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, 
             C[5] = -tt * om;
         }
     }
-    // combined coefficients of the stage outputs
     double A0[6], A1[6];
 #pragma unroll
     for (int j = 0; j < 6; j++) {
@@ -587,61 +694,35 @@ __device__ __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, 
         else            { A0[j] = (4.0 / 3.0) * fma(-2.0, Ch[j], Cd[j]); A1[j] = 0.0; }
     }
 
-    // moment vectors multiplying the coefficients (all integrated against u psi)
     double acc0[NV], acc1[NV];
-    {
-        double one[NV], M1[NV], M2[NV], M3[NV];
 #pragma unroll
-        for (int k = 0; k < NV; k++) one[k] = k == 0 ? 1.0 : 0.0;
-        Gm<DIM, 1, 0>(one, mc, M1);
-        Gm<DIM, 1, 0>(Ab, mc, M3);
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            acc0[k] = rc * fma(A0[0], M1[k], A0[2] * M3[k]);
-            acc1[k] = rc * fma(A1[0], M1[k], A1[2] * M3[k]);
-        }
-        if (tau != 0.0) {
-            Gm<DIM, 2, 0>(ab1, mc, M2);
-            if constexpr (DIM == 2) {
-                Gm<DIM, 1, 1>(ab2, mc, t1);
-#pragma unroll
-                for (int k = 0; k < NV; k++) M2[k] += t1[k];
-            }
-#pragma unroll
-            for (int k = 0; k < NV; k++) {
-                acc0[k] = fma(rc * A0[1], M2[k], acc0[k]);
-                acc1[k] = fma(rc * A1[1], M2[k], acc1[k]);
-            }
-        }
+    for (int k = 0; k < NV; k++) {
+        acc0[k] = fma(A0[0], M1[k], A0[2] * M3[k]);
+        acc1[k] = fma(A1[0], M1[k], A1[2] * M3[k]);
     }
     if (tau != 0.0) {
-        // non-equilibrium initial parts: left state over u > 0, right state over u < 0
-        // (time slopes from <a1 u + a2 v + A> = 0, Eq. (9), with full-line moments)
+        // (abar1 u + abar2 v) g0 term: Pi'(Wc) Wcx + Sigma'(Wc) Wcy
+        double M2[NV];
+        pi_sigma_dir<DIM>(sc, Wcx, Wcy, fc.gm1, fc.K, M2);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            acc0[k] = fma(A0[1], M2[k], acc0[k]);
+            acc1[k] = fma(A1[1], M2[k], acc1[k]);
+        }
+        // non-equilibrium initial parts: left state over u > 0, right state over u < 0, with the
+        // time slope A from the compatibility condition <a1 u + a2 v + A> = 0 (Eq. (9))
 #pragma unroll
         for (int side = 0; side < 2; side++) {
+            const MState<DIM>& st = side == 0 ? sl : sr;
             const Mom<DIM>& mh = side == 0 ? ml : mr;
             const double* a1 = side == 0 ? a1l : a1r;
             const double* a2 = side == 0 ? a2l : a2r;
-            const double rs = side == 0 ? rl : rr;
-            Mom<DIM> mf;
-            if (side == 0) full_moments<DIM>(Ul, Vl, ll, K, mf);
-            else full_moments<DIM>(Ur, Vr, lr, K, mf);
-            double As[NV], L4[NV], L5[NV], L6[NV];
-            Gm<DIM, 1, 0>(a1, mf, t1);
-            if constexpr (DIM == 2) {
-                Gm<DIM, 0, 1>(a2, mf, t2);
+            const double* L4 = side == 0 ? pl1 : pr1;
+            double Wt[NV], As[NV], L5[NV], L6[NV];
+            w_t<DIM>(st, side == 0 ? Wlx : Wrx, side == 0 ? Wly : Wry, fc.gm1, Wt);
 #pragma unroll
-                for (int k = 0; k < NV; k++) b[k] = -(t1[k] + t2[k]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < NV; k++) b[k] = -t1[k];
-            }
-            if (side == 0) slope_solve<DIM>(b, Ul, Vl, ll, K, As);
-            else slope_solve<DIM>(b, Ur, Vr, lr, K, As);
-            double one[NV];
-#pragma unroll
-            for (int k = 0; k < NV; k++) one[k] = k == 0 ? 1.0 : 0.0;
-            Gm<DIM, 1, 0>(one, mh, L4);
+            for (int k = 0; k < NV; k++) b[k] = Wt[k] * st.ri;
+            slope_solve<DIM>(b, st, As);
             Gm<DIM, 2, 0>(a1, mh, L5);
             if constexpr (DIM == 2) {
                 Gm<DIM, 1, 1>(a2, mh, t1);
@@ -651,8 +732,8 @@ __device__ __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, 
             Gm<DIM, 1, 0>(As, mh, L6);
 #pragma unroll
             for (int k = 0; k < NV; k++) {
-                acc0[k] = fma(rs, fma(A0[3], L4[k], fma(A0[4], L5[k], A0[5] * L6[k])), acc0[k]);
-                acc1[k] = fma(rs, fma(A1[3], L4[k], fma(A1[4], L5[k], A1[5] * L6[k])), acc1[k]);
+                acc0[k] = fma(st.rho, fma(A0[3], L4[k], fma(A0[4], L5[k], A0[5] * L6[k])), acc0[k]);
+                acc1[k] = fma(st.rho, fma(A1[3], L4[k], fma(A1[4], L5[k], A1[5] * L6[k])), acc1[k]);
             }
         }
     }

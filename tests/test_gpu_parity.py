@@ -1,10 +1,14 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU oracle on the
 same seeded inputs.
 
-Per step, from the identical input state: identical time step, bit-identical
-troubled flags of every pass (normal and tangential, both stages, both sweeps),
-and conservative state within 1e-11 relative (per component, relative to the
-component's largest magnitude).  At the final time of smooth runs: within 1e-9.
+Per step, from the identical input state: identical time step; bit-identical
+troubled flags of every pass (normal and tangential, both sweeps) wherever both
+sides decide on identical inputs (the first stage, and the second stage when
+the GPU is fed the oracle's W*); in the actual second stage, whose input W* the
+two sides compute to round-off, a flag may differ only where the decision is
+decided by round-off; conservative state within 1e-11 relative (per component,
+relative to the component's largest magnitude).  At the final time of smooth
+runs: within 1e-9.
 """
 import numpy as np
 import pytest
@@ -26,8 +30,11 @@ def rel_diff(a, b):
     return float(np.max(np.abs(a - b).max(axis=1) / scale))
 
 
-def gpu_step(cfg, W, t0=0.0):
-    s = hgks.Solver(cfg)
+def gpu_step(cfg, W, t0=0.0, dt=None):
+    c = dict(cfg)
+    if dt is not None:
+        c["fixed_dt"] = dt
+    s = hgks.Solver(c)
     s.hgks_set_flag_capture(True)
     s.hgks_set_state(np.ascontiguousarray(W), t0)
     n = s.hgks_step(1e300, 1)
@@ -44,13 +51,34 @@ def gpu_step(cfg, W, t0=0.0):
 
 
 def check_step(cfg, W, label=""):
+    """One step from the same state on both sides.
+
+    * dt and the first-stage flags (computed from identical inputs) must be identical;
+    * the second stage runs on W*, which the two sides compute to round-off: the GPU's
+      stage code fed the oracle's W* must reproduce the oracle's second-stage flags bit for
+      bit, and in the actual run a second-stage flag may differ only where the oracle's
+      decision is decided by round-off (robustness ratio < 1: Step 3 divides two differences
+      that vanish on locally flat data);
+    * the state after the step must agree within 1e-11.
+    """
     Wg, st, fg = gpu_step(cfg, W)
-    Wo, dt, fo = oracle.step_flags(cfg, W)
+    Wstar = np.zeros_like(np.ascontiguousarray(W))
+    Wo, dt, fo, mo = oracle.step_flags(cfg, W, margins=True, wstar=Wstar)
     assert st["last_dt"] == dt, (label, st["last_dt"], dt)
     assert set(fg) == set(fo)
     for key in fo:
-        mism = int(np.count_nonzero(fg[key] != fo[key]))
-        assert mism == 0, (label, key, mism)
+        diff = fg[key] != fo[key]
+        if key[0] == 0:
+            assert int(diff.sum()) == 0, (label, key, int(diff.sum()))
+        else:
+            robust = diff & (mo[key] >= 1.0)
+            assert int(robust.sum()) == 0, (label, key, "robust decision differs", np.argwhere(robust)[:4])
+            assert int(diff.sum()) <= max(2, diff.size // 100), (label, key, int(diff.sum()))
+    _, _, f2 = gpu_step(cfg, Wstar, dt=dt)
+    for key in fo:
+        if key[0] == 1:
+            k0 = (0, key[1], key[2])
+            assert np.array_equal(f2[k0], fo[key]), (label, "stage-2 logic on identical W*", key)
     err = rel_diff(Wg, Wo)
     assert err <= STEP_TOL, (label, err)
     return Wo, st, fo, err
