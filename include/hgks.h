@@ -162,6 +162,42 @@ size_t hgks_footprint_bytes(const hgks_config* cfg);
  * with a latched error is left unchanged.  stream: cudaStream_t cast to void*. */
 int hgks_batch_step(hgks_solver* const* solvers, int n, const double* t_end, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free single step.                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the static device scratch used by hgks_step_noalloc (8 MiB). */
+#define HGKS_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+
+/* One S2O4 step of the state W_in into W_out, for callers that must not
+ * allocate device memory: a process whose memory manager already owns the
+ * GPU's memory (a framework's caching allocator, an embedding host that hands
+ * the library only buffers it owns), or a loop that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.  The paper has no
+ * counterpart; the arithmetic is exactly that of hgks_step on a solver created
+ * from *cfg (same kernels, dt from the CFL rule or cfg->fixed_dt, no t_end
+ * clipping).
+ *
+ * W_in, W_out: device memory of the current device, [nv][ny][nx] FP64 as
+ * everywhere in this ABI, owned by the caller; they may be the same buffer.
+ * stream: cudaStream_t cast to void* (NULL = default stream).  The call
+ * enqueues the work and returns; W_out is ready when the stream reaches it.
+ *
+ * Every intermediate buffer lives in one file-scope device array of
+ * HGKS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits; no cudaMalloc, cudaFree or other allocation is made.  A
+ * configuration whose buffers do not fit (hgks_footprint_bytes(cfg) greater
+ * than HGKS_NOALLOC_SCRATCH_BYTES: square 2D grids above 93 x 93 cells, 1D
+ * grids above 37 112 cells) is rejected with HGKS_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU race and corrupt each
+ * other, so issue them one after another (for example on one stream).  Each
+ * call clears the array before use.
+ * Errors: HGKS_EINVAL (bad config, NULL buffer, grid too large; message in
+ * hgks_last_error(NULL)), HGKS_ECUDA. */
+int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

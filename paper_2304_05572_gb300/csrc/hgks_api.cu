@@ -464,3 +464,112 @@ extern "C" int hgks_batch_step(hgks_solver* const* solvers, int n, const double*
     }
     return HGKS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free single step (hgks_step_noalloc): the same S2O4 step as a solver
+// performs, with every intermediate buffer carved out of one file-scope device
+// array instead of a cudaMalloc'd pool.  The array is part of the library image,
+// so every GPU that loads the library keeps HGKS_NOALLOC_SCRATCH_BYTES of it
+// until the process exits.
+#include <mutex>
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[HGKS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices];   // device address of the array, per device (host stand-in is not usable)
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, void* stream)
+{
+    int st = validate(cfg, g_create_err);
+    if (st != HGKS_OK) return st;
+    if (!W_in || !W_out) { set_err(g_create_err, "W_in and W_out must be device pointers"); return HGKS_EINVAL; }
+    Params P;
+    Sweep sw[2];
+    fill_params(cfg, P);
+    fill_sweeps(cfg, P, sw);
+    Layout L = plan(cfg, P, sw);
+    if (L.total > (size_t)HGKS_NOALLOC_SCRATCH_BYTES) {
+        set_err(g_create_err, "grid needs %zu bytes of scratch; the static scratch of hgks_step_noalloc holds %zu",
+                L.total, (size_t)HGKS_NOALLOC_SCRATCH_BYTES);
+        return HGKS_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        set_err(g_create_err, "no usable current CUDA device (%s)", cudaGetErrorString(e));
+        return HGKS_ECUDA;
+    }
+    void* base = nullptr;
+    {
+        // one-time set-up per device, with that device current: the address of the array
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                set_err(g_create_err, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+                return HGKS_ECUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    // a solver object on the stack whose buffers all live in the static array
+    hgks_solver s;
+    s.cfg = *cfg;
+    s.P = P;
+    s.sw[0] = sw[0];
+    s.sw[1] = sw[1];
+    s.stream = (cudaStream_t)stream;
+    s.device = dev;
+    s.pool = base;
+    s.pool_bytes = L.total;
+    s.ctrl_host = nullptr;
+    memset(s.cap, 0, sizeof(s.cap));
+    s.capture = 0;
+    s.launches = 0;
+    s.timing = 0;
+    s.err[0] = 0;
+    char* b = (char*)base;
+    s.W = (double*)(b + L.off_W);
+    s.Ws = (double*)(b + L.off_Ws);
+    s.Acc = (double*)(b + L.off_Acc);
+    s.ctrl = (Ctrl*)(b + L.off_ctrl);
+    for (int d = 0; d < cfg->dim; d++) {
+        Sweep& S = s.sw[d];
+        S.line = (double*)(b + L.off_line);
+        S.gp = cfg->dim == 2 ? (double*)(b + L.off_gp) : nullptr;
+        S.rawN = (uint8_t*)(b + L.off_rawN[d]);
+        S.flagN = (uint8_t*)(b + L.off_flagN[d]);
+        S.itemsN = (uint32_t*)(b + L.off_itemsN[d]);
+        if (cfg->dim == 2) {
+            S.rawT = (uint8_t*)(b + L.off_rawT[d]);
+            S.flagT = (uint8_t*)(b + L.off_flagT[d]);
+            S.itemsT = (uint32_t*)(b + L.off_itemsT[d]);
+        }
+        S.flux = (double*)(b + L.off_flux[d]);
+    }
+    const GridGeom& g = s.P.g;
+    // the array keeps the previous call's contents: start every call from zero
+    e = cudaMemsetAsync(base, 0, L.total, s.stream);
+    for (int k = 0; k < g.nv && e == cudaSuccess; k++)
+        e = cudaMemcpy2DAsync(s.W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
+                              W_in + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),
+                              (size_t)g.nx * sizeof(double), (size_t)g.ny, cudaMemcpyDeviceToDevice, s.stream);
+    if (e == cudaSuccess) e = launch_set_time(&s, 0.0);
+    if (e == cudaSuccess) e = launch_step(&s, 1e300);
+    for (int k = 0; k < g.nv && e == cudaSuccess; k++)
+        e = cudaMemcpy2DAsync(W_out + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),
+                              s.W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
+                              (size_t)g.nx * sizeof(double), (size_t)g.ny, cudaMemcpyDeviceToDevice, s.stream);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "hgks_step_noalloc: %s", cudaGetErrorString(e));
+        return HGKS_ECUDA;
+    }
+    return HGKS_OK;
+}

@@ -32,7 +32,7 @@ EXPORTED = [
     "hgks_config_default", "hgks_create_solver", "hgks_destroy_solver", "hgks_set_state", "hgks_step",
     "hgks_get_state", "hgks_get_time", "hgks_get_stats", "hgks_set_flag_capture", "hgks_flags_size",
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
-    "hgks_batch_step",
+    "hgks_batch_step", "hgks_step_noalloc",
 ]
 
 
@@ -97,6 +97,7 @@ def lib():
         L.hgks_footprint_bytes.argtypes = [ctypes.POINTER(hgks_config)]
         L.hgks_footprint_bytes.restype = ctypes.c_size_t
         L.hgks_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, vp]
+        L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp]
         _lib = L
         return L
 
@@ -263,3 +264,17 @@ def run(cfg: dict, W, t_end: float, max_steps: int = 1 << 30, t0: float = 0.0):
         return s.hgks_get_state(), s.hgks_get_time(), n
     finally:
         s.hgks_destroy_solver()
+
+
+def hgks_step_noalloc(cfg: dict, W_in, W_out, stream=None):
+    """One S2O4 step W_in -> W_out (CUDA float64 tensors [nv][ny][nx]) without any device
+    allocation: the intermediates live in the library's static scratch (see include/hgks.h)."""
+    c = make_config(cfg)
+    pin, din = _ptr(W_in)
+    pout, dout = _ptr(W_out)
+    if not (din and dout):
+        raise ValueError("hgks_step_noalloc takes device tensors")
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rc = lib().hgks_step_noalloc(ctypes.byref(c), pin, pout, ctypes.c_void_p(st or 0))
+    if rc != HGKS_OK:
+        raise HGKSError(rc, lib().hgks_last_error(None).decode())
