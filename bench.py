@@ -151,6 +151,115 @@ def run_reference(args, rank, world):
     return 0
 
 
+def bench_batched(args, torch, hgks, P):
+    """Independent four-quadrant Riemann solves (sides log-uniform in [64, 1024]): one
+    launch set per solve (serial on one stream) against shared batched launches (CUDA
+    graph replay, autotuned block sizes).  Both forms advance every solve by the same
+    steps from the same state and must give the same bits.  A solve whose state turns
+    non-physical (the scheme has no positivity limiter) stops in both forms at the same
+    step; the work counted is the cell-stages actually advanced."""
+    cases = P.batched_workload(args.solves)
+    stream = torch.cuda.Stream()
+    solvers = [hgks.Solver(cfg, stream=stream) for cfg, _ in cases]
+    ncell = [int(np.prod(W.shape[1:])) for _, W in cases]
+    warm = max(args.warmup, 4)          # the autotuner takes 4 steps
+
+    def reset():
+        for s, (cfg, W) in zip(solvers, cases):
+            s.hgks_set_state(np.ascontiguousarray(W))
+
+    def steps_now():
+        return [int(s.hgks_get_stats()["steps"]) for s in solvers]
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
+    # one solve per launch set
+    reset()
+    for s in solvers:
+        s.hgks_step(1e9, warm, wait=False)
+    s0 = steps_now()
+    t_plain = timed(lambda: [s.hgks_step(1e9, args.steps, wait=False) for s in solvers])
+    s1 = steps_now()
+    plain_final = [s.hgks_get_state() for s in solvers]
+    work_plain = sum(c * 2 * (b - a) for c, a, b in zip(ncell, s0, s1))
+    # batched
+    reset()
+    batch = hgks.Batch(solvers, stream=stream)
+    te = [1e9] * len(solvers)
+    batch.hgks_batch_step(te, nsteps=warm, graph=True, autotune=True)
+    batch.hgks_batch_sync()
+    b0 = steps_now()
+    t_batch = timed(lambda: batch.hgks_batch_step(te, nsteps=args.steps, graph=True))
+    _, failed = batch.hgks_batch_sync()
+    b1 = steps_now()
+    work_batch = sum(c * 2 * (b - a) for c, a, b in zip(ncell, b0, b1))
+    tpb, _ = batch.hgks_batch_info()
+    same = b1 == s1 and all(np.array_equal(s.hgks_get_state(), ref, equal_nan=True)
+                            for s, ref in zip(solvers, plain_final))
+    batch.hgks_batch_destroy()
+    for s in solvers:
+        s.hgks_destroy_solver()
+    line = {"metric": METRIC, "workload": "batched: %d four-quadrant Riemann solves, sides log-uniform 64..1024 "
+            "(PCG64 seed %d), %d cells in all, %d timed S2O4 steps each after %d untimed"
+            % (len(cases), P.BATCH_SEED, sum(ncell), args.steps, warm),
+            "unit": UNIT, "value": work_batch / t_batch / 1e6, "plain_value": work_plain / t_plain / 1e6,
+            "speedup_vs_plain": (work_batch / t_batch) / (work_plain / t_plain),
+            "batched_ms_per_step": t_batch / args.steps * 1e3, "plain_ms_per_step": t_plain / args.steps * 1e3,
+            "cell_stages_timed": work_batch, "failed_solves": failed, "bitwise_equal_to_plain": bool(same),
+            "autotuned_block_sizes": tpb, "l2": "working set (%.1f GB of state) far above L2" % (
+                sum(ncell) * 4 * 8 * 3 / 1e9), "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+    print(json.dumps(line), flush=True)
+
+
+def bench_served(args, torch, hgks, P):
+    """Seeded Poisson stream of mixed solves through the continuous-batching server, and
+    the same trace served one solve at a time (FIFO, each solve alone on the GPU)."""
+    from paper_2304_05572_gb300 import server
+    trace = P.served_trace(n_requests=args.requests, rate=args.rate, max_1d=args.max_1d, max_2d=args.max_2d,
+                           max_ns=args.max_ns)
+    stream = torch.cuda.Stream()
+    srv = server.Server(budget_bytes=args.budget_gb * 1e9, stream=stream, steps_per_iter=args.steps_per_iter,
+                        autotune=False)
+    res = srv.run(trace)
+    served_wall = srv.wall
+    lat = np.array([res[r["id"]]["latency"] for r in trace])
+    work = sum(res[r["id"]]["cells"] * 2 * res[r["id"]]["steps"] for r in trace)
+    # plain: FIFO, one solve at a time, each alone
+    t0 = time.perf_counter()
+    done_at = {}
+    same = True
+    clock = 0.0
+    for r in trace:
+        start = max(clock, r["arrival"])
+        w0 = time.perf_counter()
+        out, st = server.run_alone(r, stream=stream)
+        dur = time.perf_counter() - w0
+        clock = start + dur
+        done_at[r["id"]] = clock - r["arrival"]
+        same = same and np.array_equal(out, res[r["id"]]["W"])
+    plain_wall = time.perf_counter() - t0
+    plain_lat = np.array([done_at[r["id"]] for r in trace])
+    line = {"metric": METRIC, "workload": "served: %d requests, Poisson rate %.0f/s (PCG64 seed %d), mix of 1D shock "
+            "tubes <= %d cells, 2D Riemann/vortex <= %d^2, 2D NS shock tubes <= %dx%d, t_end ~ U[0.05, 0.3], "
+            "budget %.0f GB" % (len(trace), args.rate, P.SERVE_SEED, args.max_1d, args.max_2d, args.max_ns,
+                                args.max_ns // 2, args.budget_gb),
+            "unit": UNIT, "value": work / served_wall / 1e6, "plain_value": work / plain_wall / 1e6,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "plain_p50_latency_s": float(np.percentile(plain_lat, 50)),
+            "plain_p99_latency_s": float(np.percentile(plain_lat, 99)),
+            "served_wall_s": served_wall, "plain_wall_s": plain_wall, "iterations": srv.iterations,
+            "peak_resident_solves": srv.peak_resident, "results_bitwise_equal_alone": bool(same),
+            "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,6 +268,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served"])
+    ap.add_argument("--solves", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--max-1d", type=int, default=4096)
+    ap.add_argument("--max-2d", type=int, default=512)
+    ap.add_argument("--max-ns", type=int, default=512)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--steps-per-iter", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -182,6 +300,10 @@ def main():
     from paper_2304_05572_gb300 import hgks, problems as P
 
     torch.cuda.set_device(local_rank)
+    if args.workload == "batched":
+        return bench_batched(args, torch, hgks, P)
+    if args.workload == "served":
+        return bench_served(args, torch, hgks, P)
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
@@ -207,6 +329,7 @@ def main():
     torch.cuda.synchronize()
     solver.hgks_set_timing(True)
     solver.hgks_get_timing()              # drop warm-up records (timing starts now)
+    launches0 = int(solver.hgks_get_stats()["launches"])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0) as clk:
@@ -255,7 +378,7 @@ def main():
 
     # ---- dominant kernel roofline (FP64 ALU)
     flux_ms, flux_calls = timing.get("gks_flux", (0.0, 0))
-    launches = int(stats.get("launches", 0))
+    launches = int(stats.get("launches", 0)) - launches0     # kernels of the timed steps only
     roofline = None
     if flux_calls:
         avg_ms = flux_ms / flux_calls

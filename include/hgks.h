@@ -149,18 +149,54 @@ const char* hgks_last_error(const hgks_solver* s);
 size_t hgks_footprint_bytes(const hgks_config* cfg);
 
 /* ------------------------------------------------------------------------ */
-/* Batched execution: many independent solvers advanced together.            */
+/* Batched execution: many independent solvers advanced by the same launches.*/
 /* ------------------------------------------------------------------------ */
 
-/* Advance every solver in solvers[0..n-1] by one S2O4 step each (each with its
- * own dt and its own t_end), enqueued on the given stream as one set of
- * multi-solve launches per stage (one launch per kernel class, whose blocks are
- * distributed over all solvers' tiles), instead of one launch set per solver.
- * Results are identical to stepping each solver alone.  All solvers must live
- * on the current device; their own streams are ordered before and after the
- * batch by events.  t_end[i] as in hgks_step; a solver already at its t_end or
- * with a latched error is left unchanged.  stream: cudaStream_t cast to void*. */
-int hgks_batch_step(hgks_solver* const* solvers, int n, const double* t_end, void* stream);
+typedef struct hgks_batch hgks_batch;
+
+#define HGKS_BATCH_GRAPH 1      /* replay one captured batched step (needs a non-NULL stream) */
+#define HGKS_BATCH_AUTOTUNE 2   /* choose the block size of each kernel class on the first steps (see hgks_batch_step) */
+
+/* Group n >= 1 solvers of the same dimension on the current device.  One
+ * batched step issues one launch per kernel class (40 per step in 2D) whose
+ * blocks cover every solver's interfaces; each block works for exactly one
+ * solver with that solver's own arithmetic, so every result is bit-identical
+ * to stepping the solver alone.  The solvers keep their own state, dt, time and
+ * counters; they must stay alive, and must not be stepped on their own, while
+ * the batch exists.  stream: cudaStream_t cast to void* for all batched work.
+ * The batch's own device memory is O(n) (descriptors, block tables).
+ * The paper describes one solve at a time; batching is this library's way of
+ * filling one GPU with many small solves.  Errors: HGKS_EINVAL, HGKS_ENOMEM, HGKS_ECUDA. */
+int hgks_batch_create(hgks_solver* const* solvers, int n, void* stream, hgks_batch** out);
+
+/* Enqueue nsteps batched S2O4 steps.  t_end (length n, may be NULL to keep the
+ * previous values; initially 0) is each solver's end time with hgks_step's
+ * clipping rule; solvers at their end time or with a latched error are left
+ * unchanged by further steps.  flags: HGKS_BATCH_GRAPH | HGKS_BATCH_AUTOTUNE.
+ * With HGKS_BATCH_AUTOTUNE on a batch not tuned yet, the first (up to) 4 of the
+ * nsteps steps are taken one at a time with a wait after each: one with the
+ * default block sizes, then one with each of three candidate sizes per kernel
+ * class, timed per class with CUDA events; the fastest size of each class is
+ * kept for the rest of the batch's life.  These are real steps (results do not
+ * depend on the block size).  Otherwise the call returns after enqueueing (no
+ * wait); use hgks_batch_sync to wait.  A graph captured earlier is rebuilt
+ * after tuning. */
+int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, int flags);
+
+/* Wait for the batch's stream.  *n_active (may be NULL) = solvers that have not
+ * reached their t_end and have no latched error; *n_failed (may be NULL) =
+ * solvers with a latched HGKS_ENONPHYSICAL (they stopped at the step that
+ * produced the state, exactly as hgks_step would; hgks_get_stats tells which).
+ * A failed solver does not stop the others, and is not an error of the batch:
+ * returns HGKS_OK unless a CUDA call failed (HGKS_ECUDA). */
+int hgks_batch_sync(hgks_batch* b, int* n_active, int* n_failed);
+
+/* Block size chosen for each kernel class (up to cap entries) and the number of
+ * batched steps enqueued so far; returns the number of kernel classes. */
+int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long* steps_enqueued);
+
+const char* hgks_batch_last_error(const hgks_batch* b);
+void hgks_batch_destroy(hgks_batch* b);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free single step.                                              */

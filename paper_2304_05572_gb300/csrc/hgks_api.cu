@@ -442,28 +442,205 @@ extern "C" int hgks_get_timing(hgks_solver* s, int cap, const char** names, doub
     return n;
 }
 
-extern "C" int hgks_batch_step(hgks_solver* const* solvers, int n, const double* t_end, void* stream)
+// ---------------------------------------------------------------------------
+// Batched execution: one launch per kernel class for all solvers of a batch.
+struct hgks_batch {
+    int n = 0, dim = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<hgks_solver*> solvers;
+    SolveDesc* d_desc = nullptr;
+    int* d_boff = nullptr;
+    double* d_tend = nullptr;
+    double* h_tend = nullptr;
+    BatchPlan plan;
+    int tuned = 0;
+    cudaEvent_t ev[2 * BK_COUNT];
+    cudaEvent_t tend_ev = nullptr;   // marks the last copy out of h_tend
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long steps_enqueued = 0;
+    char err[512];
+};
+
+namespace {
+
+int batch_upload_plan(hgks_batch* b, const int* tpb)
 {
-    if (n < 0 || (n > 0 && (!solvers || !t_end))) return HGKS_EINVAL;
-    cudaStream_t bs = (cudaStream_t)stream;
+    std::vector<SolveDesc> h(b->n);
+    std::vector<const SolveDesc*> ptrs(b->n);
+    for (int i = 0; i < b->n; i++) { batch_fill_desc(b->solvers[i], h[i]); ptrs[i] = &h[i]; }
+    batch_plan(ptrs, b->dim, tpb, b->plan);
+    cudaError_t e = cudaMemcpyAsync(b->d_boff, b->plan.boff.data(), b->plan.boff.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { set_err(b->err, "plan upload failed: %s", cudaGetErrorString(e)); return HGKS_ECUDA; }
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return HGKS_OK;
+}
+
+}  // namespace
+
+extern "C" int hgks_batch_create(hgks_solver* const* solvers, int n, void* stream, hgks_batch** out)
+{
+    if (!out || n < 1 || !solvers) { set_err(g_create_err, "need at least one solver"); return HGKS_EINVAL; }
+    *out = nullptr;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    int dim = 0;
     for (int i = 0; i < n; i++) {
-        hgks_solver* s = solvers[i];
-        if (!s) return HGKS_EINVAL;
-        cudaEvent_t e;
-        CUDA_TRY(s, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        CUDA_TRY(s, cudaEventRecord(e, s->stream));
-        CUDA_TRY(s, cudaStreamWaitEvent(bs, e, 0));
-        cudaStream_t own = s->stream;
-        s->stream = bs;
-        cudaError_t err = launch_step(s, t_end[i]);
-        s->stream = own;
-        if (err != cudaSuccess) { cudaEventDestroy(e); set_err(s->err, "launch failed: %s", cudaGetErrorString(err)); return HGKS_ECUDA; }
-        CUDA_TRY(s, cudaEventRecord(e, bs));
-        CUDA_TRY(s, cudaStreamWaitEvent(own, e, 0));
-        cudaEventDestroy(e);
+        if (!solvers[i]) { set_err(g_create_err, "solver %d is NULL", i); return HGKS_EINVAL; }
+        if (i == 0) dim = solvers[i]->cfg.dim;
+        if (solvers[i]->cfg.dim != dim) { set_err(g_create_err, "all solvers of a batch must have the same dimension"); return HGKS_EINVAL; }
+        if (solvers[i]->device != dev) { set_err(g_create_err, "solver %d lives on another device", i); return HGKS_EINVAL; }
+    }
+    hgks_batch* b = new (std::nothrow) hgks_batch();
+    if (!b) return HGKS_ENOMEM;
+    b->n = n; b->dim = dim; b->device = dev; b->stream = (cudaStream_t)stream;
+    b->solvers.assign(solvers, solvers + n);
+    b->err[0] = 0;
+    for (int i = 0; i < n; i++) cudaStreamSynchronize(solvers[i]->stream);
+    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(SolveDesc) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_boff, sizeof(int) * (size_t)BK_COUNT * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tend, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tend, sizeof(double) * n);
+    for (int k = 0; k < 2 * BK_COUNT && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tend_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "batch allocation failed: %s", cudaGetErrorString(e));
+        hgks_batch_destroy(b);
+        return HGKS_ENOMEM;
+    }
+    std::vector<SolveDesc> h(n);
+    for (int i = 0; i < n; i++) { batch_fill_desc(solvers[i], h[i]); b->h_tend[i] = 0.0; }
+    e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(SolveDesc) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tend, b->h_tend, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) { set_err(g_create_err, "batch upload failed: %s", cudaGetErrorString(e)); hgks_batch_destroy(b); return HGKS_ECUDA; }
+    int st = batch_upload_plan(b, kBatchTpbDefault);
+    if (st != HGKS_OK) { set_err(g_create_err, "%s", b->err); hgks_batch_destroy(b); return st; }
+    *out = b;
+    return HGKS_OK;
+}
+
+extern "C" void hgks_batch_destroy(hgks_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int k = 0; k < 2 * BK_COUNT; k++) if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    if (b->tend_ev) cudaEventDestroy(b->tend_ev);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_boff) cudaFree(b->d_boff);
+    if (b->d_tend) cudaFree(b->d_tend);
+    if (b->h_tend) cudaFreeHost(b->h_tend);
+    delete b;
+}
+
+extern "C" int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, int flags)
+{
+    if (!b || nsteps < 0) return HGKS_EINVAL;
+    if (t_end) {
+        for (int i = 0; i < b->n; i++)
+            if (!std::isfinite(t_end[i])) { set_err(b->err, "t_end[%d] is not finite", i); return HGKS_EINVAL; }
+        // the pinned staging array may still be read by the previous call's copy: wait for it
+        CUDA_TRY(b, cudaEventSynchronize(b->tend_ev));
+        for (int i = 0; i < b->n; i++) b->h_tend[i] = t_end[i];
+        CUDA_TRY(b, cudaMemcpyAsync(b->d_tend, b->h_tend, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(b, cudaEventRecord(b->tend_ev, b->stream));
+    }
+    int left = nsteps;
+    if ((flags & HGKS_BATCH_AUTOTUNE) && !b->tuned && left > 0) {
+        // try three block sizes per kernel class on live steps (the per-item arithmetic does not
+        // depend on the block size), then keep the fastest size of each class.  One untimed step
+        // with the default sizes first loads every batched kernel.
+        CUDA_TRY(b, batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, nullptr));
+        b->steps_enqueued++;
+        left--;
+        static const int cand_small[3] = {64, 128, 256};
+        static const int cand_big[3] = {128, 256, 512};
+        double best_ms[BK_COUNT];
+        int best_tpb[BK_COUNT];
+        for (int c = 0; c < BK_COUNT; c++) { best_ms[c] = 1e300; best_tpb[c] = kBatchTpbDefault[c]; }
+        for (int k = 0; k < 3 && left > 0; k++) {
+            int tpb[BK_COUNT];
+            for (int c = 0; c < BK_COUNT; c++) {
+                bool heavy_regs = (c >= BK_FLUX && c < BK_FLUX + 2) || (c >= BK_NAO && c < BK_NAO + 2) || (c >= BK_TAO && c < BK_TAO + 2);
+                tpb[c] = c == BK_CTRL ? 32 : (heavy_regs ? cand_small[k] : cand_big[k]);
+            }
+            int st = batch_upload_plan(b, tpb);
+            if (st != HGKS_OK) return st;
+            CUDA_TRY(b, batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, b->ev));
+            CUDA_TRY(b, cudaStreamSynchronize(b->stream));
+            b->steps_enqueued++;
+            left--;
+            for (int c = 0; c < BK_COUNT; c++) {
+                // classes without launches in this dimension (and the control kernels) carry no events
+                if (c == BK_CTRL || b->plan.nblk[c] == 0) continue;
+                float ms = 0.0f;
+                cudaError_t qe = cudaEventElapsedTime(&ms, b->ev[2 * c], b->ev[2 * c + 1]);
+                if (qe != cudaSuccess) { (void)cudaGetLastError(); continue; }
+                if (ms < best_ms[c]) {
+                    best_ms[c] = ms;
+                    best_tpb[c] = tpb[c];
+                }
+            }
+        }
+        int st = batch_upload_plan(b, best_tpb);
+        if (st != HGKS_OK) return st;
+        b->tuned = 1;
+    }
+    const bool use_graph = (flags & HGKS_BATCH_GRAPH) && b->stream != nullptr;
+    for (int k = 0; k < left; k++) {
+        if (use_graph) {
+            if (!b->exec) {
+                CUDA_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, nullptr);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    set_err(b->err, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+                    return HGKS_ECUDA;
+                }
+                CUDA_TRY(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+            }
+            CUDA_TRY(b, cudaGraphLaunch(b->exec, b->stream));
+        } else {
+            CUDA_TRY(b, batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, nullptr));
+        }
+        b->steps_enqueued++;
     }
     return HGKS_OK;
 }
+
+extern "C" int hgks_batch_sync(hgks_batch* b, int* n_active, int* n_failed)
+{
+    if (!b) return HGKS_EINVAL;
+    for (int i = 0; i < b->n; i++)
+        CUDA_TRY(b, cudaMemcpyAsync(b->solvers[i]->ctrl_host, b->solvers[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    int active = 0, failed = 0;
+    for (int i = 0; i < b->n; i++) {
+        const Ctrl& c = *b->solvers[i]->ctrl_host;
+        double te = b->h_tend[i];
+        double tol = 1e-12 * (fabs(te) > 1.0 ? fabs(te) : 1.0);
+        if (c.status) failed++;
+        else if (te - c.t > tol) active++;
+    }
+    if (n_active) *n_active = active;
+    if (n_failed) *n_failed = failed;
+    return HGKS_OK;
+}
+
+extern "C" int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long* steps_enqueued)
+{
+    if (!b) return HGKS_EINVAL;
+    int m = cap < (int)BK_COUNT ? cap : (int)BK_COUNT;
+    for (int c = 0; c < m && tpb; c++) tpb[c] = b->plan.tpb[c];
+    if (steps_enqueued) *steps_enqueued = b->steps_enqueued;
+    return (int)BK_COUNT;
+}
+
+extern "C" const char* hgks_batch_last_error(const hgks_batch* b) { return b ? b->err : g_create_err; }
 
 // ---------------------------------------------------------------------------
 // Allocation-free single step (hgks_step_noalloc): the same S2O4 step as a solver

@@ -69,6 +69,31 @@ struct Params {
 
 struct TimerRec { int cls; cudaEvent_t a, b; };
 
+// One solver as seen by the batched kernels (device array, one entry per solver).
+struct SolveDesc {
+    Params P;
+    Sweep sw[2];
+    double* W;
+    double* Ws;
+    double* Acc;
+    Ctrl* ctrl;
+    double h;          // min(dx, dy): the CFL length
+};
+
+// Kernel classes of a batched step.  Classes with a sweep index have one entry per sweep.
+enum BatchClass {
+    BK_CTRL = 0, BK_DT, BK_GHX, BK_GHY,
+    BK_RAWN, BK_NORMAL = BK_RAWN + 2, BK_NAO = BK_NORMAL + 2, BK_RAWT = BK_NAO + 2, BK_TANG = BK_RAWT + 2,
+    BK_TAO = BK_TANG + 2, BK_FLUX = BK_TAO + 2, BK_UPD = BK_FLUX + 2, BK_COUNT
+};
+
+struct BatchPlan {
+    int n = 0, dim = 0;
+    int tpb[BK_COUNT];
+    int nblk[BK_COUNT];            // total blocks of each class
+    std::vector<int> boff;         // [BK_COUNT][n + 1] block offsets per solver
+};
+
 }  // namespace hgks
 
 struct hgks_solver {
@@ -105,5 +130,13 @@ extern const char* kclass_names[KC_COUNT];
 cudaError_t launch_step(hgks_solver* s, double t_end);
 cudaError_t launch_set_time(hgks_solver* s, double t0);
 int device_sm_count();
+
+// batched execution (hgks_kernels.cu)
+void batch_fill_desc(const hgks_solver* s, SolveDesc& d);
+void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* tpb, BatchPlan& plan);
+// enqueue one batched step; ev (optional, 2 * BK_COUNT events) records each class for timing
+cudaError_t batch_enqueue_step(const BatchPlan& plan, const SolveDesc* d_desc, const int* d_boff,
+                               const double* d_tend, cudaStream_t st, cudaEvent_t* ev);
+extern const int kBatchTpbDefault[BK_COUNT];
 
 }  // namespace hgks

@@ -30,13 +30,12 @@ __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
 // x ghosts on interior rows, then y ghosts over the padded width (fills corners).
 // Non-reflecting: zero-gradient copy; reflect / symmetry: mirror, normal momentum negated;
 // no-slip adiabatic: mirror, both momenta negated.
-__global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
     const GridGeom& g = P.g;
     int rowsI = g.dim == 2 ? g.ny : 1;
     long long total = (long long)g.nv * rowsI * NG * 2;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int side = (int)(id % 2); id /= 2;
     int l = (int)(id % NG) + 1; id /= NG;
@@ -58,13 +57,18 @@ __global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restri
     base[dst] = v;
 }
 
-__global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    b_ghost_x(P, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+__device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
     const GridGeom& g = P.g;
     int width = g.nx + 2 * NG;
     long long total = (long long)g.nv * width * NG * 2;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int i = (int)(id % width) - NG; id /= width;
     int side = (int)(id % 2); id /= 2;
@@ -86,6 +90,12 @@ __global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restri
     base[(long long)dst * g.pitch] = v;
 }
 
+__global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    b_ghost_y(P, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
 // ---------------------------------------------------------------- time step
 __global__ void k_begin_step(Ctrl* ctrl)
 {
@@ -100,13 +110,13 @@ __global__ void k_begin_stage(Ctrl* ctrl)
 
 // Sec. 3 preamble: dt = CFL min(h/(|U|+a), h^2/(4 nu)), h = min(dx, dy), nu = mu/rho;
 // same evaluation order as the CPU reference so that dt is reproduced exactly.
-__global__ void k_dt(Params P, const double* __restrict__ W, Ctrl* ctrl, double h)
+__device__ __forceinline__ void b_dt(const Params& P, const double* __restrict__ W, Ctrl* ctrl, double h, long long start, long long stride)
 {
     const GridGeom& g = P.g;
     int rowsI = g.dim == 2 ? g.ny : 1;
     long long n = (long long)rowsI * g.nx;
     unsigned long long best = 0x7FF0000000000000ull;
-    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+    for (long long id = start; id < n; id += stride) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
         const double* c = W + g.origin + (long long)j * g.pitch + i;
         ex rho(c[0]);
@@ -132,6 +142,12 @@ __global__ void k_dt(Params P, const double* __restrict__ W, Ctrl* ctrl, double 
     }
     if ((threadIdx.x & 31) == 0) atomicMin(&ctrl->dtmin_bits, best);
 }
+
+__global__ void k_dt(Params P, const double* __restrict__ W, Ctrl* ctrl, double h)
+{
+    b_dt(P, W, ctrl, h, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 
 __global__ void k_dt_final(Ctrl* ctrl, double cfl, double fixed_dt, double t_end, double tol)
 {
@@ -192,12 +208,11 @@ __device__ __forceinline__ const double* cellp(const Params& P, const Sweep& S, 
 }
 
 template <int NV>
-__global__ void k_raw_nflags(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__device__ __forceinline__ void b_raw_nflags(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
     int width = S.nn + 4;
     long long total = (long long)S.nlines * width;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int c = (int)(id % width), L = (int)(id / width);
     int t = L + S.tlo, n = c - 2;
@@ -217,6 +232,13 @@ __global__ void k_raw_nflags(Params P, Sweep S, const double* __restrict__ W, co
 }
 
 template <int NV>
+__global__ void k_raw_nflags(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    b_raw_nflags<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+template <int NV>
 __device__ __forceinline__ void store_line(const Params& P, const Sweep& S, int L, int m, int side, const double* val, const double* der)
 {
     long long plane = (long long)S.nlines * S.nm;
@@ -229,11 +251,10 @@ __device__ __forceinline__ void store_line(const Params& P, const Sweep& S, int 
 }
 
 template <int NV>
-__global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* ctrl, int stage)
+__device__ __forceinline__ void b_normal(const Params& P, const Sweep& S, const double* __restrict__ W, Ctrl* ctrl, int stage, long long id)
 {
     if (ctrl->done) return;
     long long total = (long long)S.nlines * S.nm;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = id < total;
     int L = 0, m = 0;
     if (active) { m = (int)(id % S.nm); L = (int)(id / S.nm); }
@@ -284,14 +305,21 @@ __global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* 
 }
 
 template <int NV>
-__global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* ctrl, int stage)
+{
+    b_normal<NV>(P, S, W, ctrl, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+template <int NV>
+__device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
 {
     if (ctrl->done) return;
     unsigned int n = ctrl->cnt[S.dir][0];
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
-    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
         uint32_t it = S.itemsN[i];
         int side = it & 1;
         long long lm = it >> 1;
@@ -322,6 +350,13 @@ __global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, con
     }
 }
 
+template <int NV>
+__global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    b_normal_ao<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+
 // ---------------------------------------------------------------- tangential passes (2D)
 __device__ __forceinline__ double lineval(const Sweep& S, int X, int k, int t, int m)
 {
@@ -329,11 +364,10 @@ __device__ __forceinline__ double lineval(const Sweep& S, int X, int k, int t, i
     return ld(S.line + (long long)(X * 4 + k) * plane + (long long)(t - S.tlo) * S.nm + m);
 }
 
-__global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
+__device__ __forceinline__ void b_raw_tflags(const Params& P, const Sweep& S, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
     long long total = (long long)(S.nt + 2) * S.nm;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int m = (int)(id % S.nm);
     int t = (int)(id / S.nm) - 1;
@@ -354,6 +388,12 @@ __global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
     }
     S.rawT[id] = bits;
 }
+
+__global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
+{
+    b_raw_tflags(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 __device__ __forceinline__ void store_gp(const Sweep& S, int t, int m, int X, const double (*v)[2], const double (*d)[2], double inv_ht)
 {
@@ -383,11 +423,10 @@ __device__ __forceinline__ void gp_positivity(const Params& P, const Sweep& S, i
     }
 }
 
-__global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
+__device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ctrl, int stage, long long id)
 {
     if (ctrl->done) return;
     long long total = (long long)S.nt * S.nm;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = id < total;
     int m = 0, t = 0;
     unsigned int bits = 0;
@@ -418,14 +457,20 @@ __global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
     }
 }
 
-__global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
+{
+    b_tang(P, S, ctrl, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+__device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
 {
     if (ctrl->done) return;
     unsigned int n = ctrl->cnt[S.dir][1];
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
-    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
         uint32_t it = S.itemsT[i];
         int X = it & 3;
         long long tm = it >> 2;
@@ -469,16 +514,21 @@ __global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const
     }
 }
 
+__global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+{
+    b_tang_ao(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+
 // ---------------------------------------------------------------- flux and update
 template <int DIM, int STAGE>
-__global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
+__device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ctrl, long long id)
 {
     if (ctrl->done) return;
     constexpr int NV = DIM + 2;
     constexpr int NGP = DIM == 2 ? 2 : 1;
     long long per = (long long)S.nt * S.nm;
     long long total = per * NGP;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int g = (int)(id / per);
     long long o = id % per;
@@ -514,18 +564,23 @@ __global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
     }
 }
 
+template <int DIM, int STAGE>
+__global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
+{
+    b_flux<DIM, STAGE>(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
 // Stage 0: W* = W^n - dF(dt/2)/dx - dG(dt/2)/dy (Eq. (19)), Acc = W^n - d(dt F^n + dt^2/6 dF^n)/dx - ...
 // Stage 1: W^{n+1} = Acc - d(dt^2/3 dF*)/dx - ... (Eqs. (20)-(22))
 template <int DIM, int STAGE>
-__global__ void k_update(Params P, Sweep Sx, Sweep Sy, const double* __restrict__ Win, double* __restrict__ Wout,
-                         double* __restrict__ Acc, Ctrl* ctrl)
+__device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const Sweep& Sy, const double* __restrict__ Win, double* __restrict__ Wout, double* __restrict__ Acc, Ctrl* ctrl, long long id)
 {
     if (ctrl->done) return;
     constexpr int NV = DIM + 2;
     const GridGeom& g = P.g;
     int rowsI = DIM == 2 ? g.ny : 1;
     long long n = (long long)rowsI * g.nx;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n) return;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
     long long cell = g.origin + (long long)j * g.pitch + i;
@@ -571,6 +626,133 @@ __global__ void k_update(Params P, Sweep Sx, Sweep Sy, const double* __restrict_
     double ke = DIM == 2 ? 0.5 * (out[1] * out[1] + out[2] * out[2]) / out[0] : 0.5 * out[1] * out[1] / out[0];
     double p = (P.gamma - 1.0) * (out[NV - 1] - ke);
     if (!(out[0] > 0.0) || !(p > 0.0) || !isfinite(out[0]) || !isfinite(p)) ctrl->status = HGKS_ENONPHYSICAL;
+}
+
+template <int DIM, int STAGE>
+__global__ void k_update(Params P, Sweep Sx, Sweep Sy, const double* __restrict__ Win, double* __restrict__ Wout,
+                         double* __restrict__ Acc, Ctrl* ctrl)
+{
+    b_update<DIM, STAGE>(P, Sx, Sy, Win, Wout, Acc, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+// ---------------------------------------------------------------- batched kernels
+// One launch per kernel class covers the blocks of every solver of a batch: block b belongs
+// to solver s with boff[s] <= b < boff[s+1] and runs that solver's kernel body on its local
+// block index.  No block mixes solvers, so every result is bit-identical to stepping alone.
+__device__ __forceinline__ int find_solve(const int* __restrict__ boff, int n, int b)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (boff[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+#define HGKS_BATCH_BLOCK()                                                              \
+    const int s_ = find_solve(boff, n, (int)blockIdx.x);                                 \
+    const SolveDesc& d = D[s_];                                                          \
+    const long long lblk_ = (long long)blockIdx.x - boff[s_];                            \
+    const long long nblk_ = (long long)(boff[s_ + 1] - boff[s_]);                         \
+    const long long id = lblk_ * blockDim.x + threadIdx.x;                               \
+    (void)nblk_; (void)id;
+
+__global__ void kb_ctrl(const SolveDesc* __restrict__ D, int n, int what, const double* __restrict__ tend)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    Ctrl* ctrl = D[s].ctrl;
+    if (what == 0) {                       // begin step
+        ctrl->dtmin_bits = 0x7FF0000000000000ull;
+        ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
+    } else if (what == 1) {                // dt final (as k_dt_final, t_end per solver)
+        const Params& P = D[s].P;
+        double t_end = tend[s];
+        double tol = 1e-12 * (fabs(t_end) > 1.0 ? fabs(t_end) : 1.0);
+        double dt = P.fixed_dt > 0.0 ? P.fixed_dt : P.cfl * __longlong_as_double((long long)ctrl->dtmin_bits);
+        int done = ctrl->status != 0 || !(t_end - ctrl->t > tol);
+        if (!done && ctrl->t + dt > t_end) dt = t_end - ctrl->t;
+        if (!done && !(dt > 0.0 && dt < 1e300)) { ctrl->status = HGKS_ENONPHYSICAL; done = 1; }
+        ctrl->dt = dt;
+        ctrl->done = done;
+    } else if (what == 2) {                // begin stage
+        ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
+    } else {                               // end step
+        if (ctrl->done) return;
+        ctrl->t += ctrl->dt;
+        ctrl->last_dt = ctrl->dt;
+        ctrl->steps += 1;
+    }
+}
+
+__global__ void kb_dt(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n)
+{
+    HGKS_BATCH_BLOCK();
+    if (d.P.fixed_dt > 0.0) return;
+    b_dt(d.P, d.W, d.ctrl, d.h, id, nblk_ * blockDim.x);
+}
+
+__global__ void kb_ghost(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int axis)
+{
+    HGKS_BATCH_BLOCK();
+    double* W = stage == 0 ? d.W : d.Ws;
+    if (axis == 0) b_ghost_x(d.P, W, d.ctrl, id);
+    else b_ghost_y(d.P, W, d.ctrl, id);
+}
+
+template <int NV>
+__global__ void kb_raw_nflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_raw_nflags<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id);
+}
+
+template <int NV>
+__global__ void kb_normal(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_normal<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, stage, id);
+}
+
+template <int NV>
+__global__ void kb_normal_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
+}
+
+__global__ void kb_raw_tflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_raw_tflags(d.P, d.sw[dir], d.ctrl, id);
+}
+
+__global__ void kb_tang(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_tang(d.P, d.sw[dir], d.ctrl, stage, id);
+}
+
+__global__ void kb_tang_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
+}
+
+template <int DIM, int STAGE>
+__global__ void __launch_bounds__(256) kb_flux(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
+{
+    HGKS_BATCH_BLOCK();
+    b_flux<DIM, STAGE>(d.P, d.sw[dir], d.ctrl, id);
+}
+
+template <int DIM, int STAGE>
+__global__ void kb_update(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n)
+{
+    HGKS_BATCH_BLOCK();
+    if (STAGE == 0) b_update<DIM, 0>(d.P, d.sw[0], d.sw[1], d.W, d.Ws, d.Acc, d.ctrl, id);
+    else b_update<DIM, 1>(d.P, d.sw[0], d.sw[1], d.Ws, d.W, d.Acc, d.ctrl, id);
 }
 
 inline unsigned int blocks_for(long long n, int tpb) { return (unsigned int)((n + tpb - 1) / tpb); }
@@ -698,6 +880,148 @@ cudaError_t launch_step(hgks_solver* s, double t_end)
     if (P.g.dim == 2) { enqueue_stage<2>(s, 0); enqueue_stage<2>(s, 1); }
     else { enqueue_stage<1>(s, 0); enqueue_stage<1>(s, 1); }
     timed(s, KC_MISC, 1, [&] { k_end_step<<<1, 1, 0, st>>>(s->ctrl); });
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- host: batched step
+const int kBatchTpbDefault[BK_COUNT] = {
+    32, 256, 256, 256,        // ctrl, dt, ghost x, ghost y
+    256, 256,                 // raw normal flags (x, y)
+    256, 256,                 // normal reconstruction
+    128, 128,                 // normal WENO-AO
+    256, 256,                 // raw tangential flags
+    256, 256,                 // tangential reconstruction
+    128, 128,                 // tangential WENO-AO
+    128, 128,                 // flux
+    256                       // update
+};
+
+void batch_fill_desc(const hgks_solver* s, SolveDesc& d)
+{
+    d.P = s->P;
+    d.sw[0] = s->sw[0];
+    d.sw[1] = s->sw[1];
+    d.W = s->W;
+    d.Ws = s->Ws;
+    d.Acc = s->Acc;
+    d.ctrl = s->ctrl;
+    d.h = s->P.g.dim == 2 ? (s->P.g.dx < s->P.g.dy ? s->P.g.dx : s->P.g.dy) : s->P.g.dx;
+}
+
+void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* tpb, BatchPlan& plan)
+{
+    const int n = (int)descs.size();
+    plan.n = n;
+    plan.dim = dim;
+    for (int c = 0; c < BK_COUNT; c++) plan.tpb[c] = tpb[c];
+    plan.boff.assign((size_t)BK_COUNT * (n + 1), 0);
+    for (int c = 0; c < BK_COUNT; c++) {
+        int* bo = plan.boff.data() + (size_t)c * (n + 1);
+        long long acc = 0;
+        for (int s = 0; s < n; s++) {
+            const SolveDesc& d = *descs[s];
+            const GridGeom& g = d.P.g;
+            const int t = tpb[c];
+            const long long cells = (long long)(dim == 2 ? g.ny : 1) * g.nx;
+            long long b = 0;
+            int dir = 0;
+            if (c >= BK_RAWN && c < BK_UPD) dir = (c - BK_RAWN) % 2;
+            const Sweep& S = d.sw[dir];
+            const bool sweep_used = dir == 0 || dim == 2;
+            switch (c >= BK_RAWN && c < BK_UPD ? BK_RAWN + ((c - BK_RAWN) / 2) * 2 : c) {
+                case BK_CTRL: b = 0; break;
+                case BK_DT: b = (cells + (long long)t * 8 - 1) / ((long long)t * 8); break;
+                case BK_GHX: b = blocks_for((long long)g.nv * (dim == 2 ? g.ny : 1) * NG * 2, t); break;
+                case BK_GHY: b = dim == 2 ? blocks_for((long long)g.nv * (g.nx + 2 * NG) * NG * 2, t) : 0; break;
+                case BK_RAWN: b = sweep_used ? blocks_for((long long)S.nlines * (S.nn + 4), t) : 0; break;
+                case BK_NORMAL: b = sweep_used ? blocks_for((long long)S.nlines * S.nm, t) : 0; break;
+                case BK_NAO: b = sweep_used ? blocks_for((long long)S.nlines * S.nm * 2, t * 8) : 0; break;
+                case BK_RAWT: b = dim == 2 ? blocks_for((long long)(S.nt + 2) * S.nm, t) : 0; break;
+                case BK_TANG: b = dim == 2 ? blocks_for((long long)S.nt * S.nm, t) : 0; break;
+                case BK_TAO: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * 4, t * 8) : 0; break;
+                case BK_FLUX: b = sweep_used ? blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t) : 0; break;
+                case BK_UPD: b = blocks_for(cells, t); break;
+            }
+            if (b < 1 && c != BK_CTRL && !(c == BK_GHY && dim == 1) && b == 0 && sweep_used) b = 1;
+            bo[s] = (int)acc;
+            acc += b;
+        }
+        bo[n] = (int)acc;
+        plan.nblk[c] = c == BK_CTRL ? (int)blocks_for(n, tpb[c]) : (int)acc;
+    }
+}
+
+cudaError_t batch_enqueue_step(const BatchPlan& plan, const SolveDesc* dd, const int* dboff, const double* dtend,
+                               cudaStream_t st, cudaEvent_t* ev)
+{
+    const int n = plan.n;
+    const int dim = plan.dim;
+    auto bo = [&](int c) { return dboff + (size_t)c * (n + 1); };
+    auto mark = [&](int c, int which) { if (ev) cudaEventRecord(ev[2 * c + which], st); };
+    auto grid = [&](int c) { return (unsigned int)plan.nblk[c]; };
+    const int tc = plan.tpb[BK_CTRL];
+    kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 0, dtend);
+    mark(BK_DT, 0);
+    if (grid(BK_DT)) kb_dt<<<grid(BK_DT), plan.tpb[BK_DT], 0, st>>>(dd, bo(BK_DT), n);
+    mark(BK_DT, 1);
+    kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 1, dtend);
+    for (int stage = 0; stage < 2; stage++) {
+        kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 2, dtend);
+        mark(BK_GHX, 0);
+        kb_ghost<<<grid(BK_GHX), plan.tpb[BK_GHX], 0, st>>>(dd, bo(BK_GHX), n, stage, 0);
+        mark(BK_GHX, 1);
+        if (dim == 2) {
+            mark(BK_GHY, 0);
+            kb_ghost<<<grid(BK_GHY), plan.tpb[BK_GHY], 0, st>>>(dd, bo(BK_GHY), n, stage, 1);
+            mark(BK_GHY, 1);
+        }
+        for (int dir = 0; dir < dim; dir++) {
+            mark(BK_RAWN + dir, 0);
+            if (dim == 2) kb_raw_nflags<4><<<grid(BK_RAWN + dir), plan.tpb[BK_RAWN + dir], 0, st>>>(dd, bo(BK_RAWN + dir), n, stage, dir);
+            else kb_raw_nflags<3><<<grid(BK_RAWN + dir), plan.tpb[BK_RAWN + dir], 0, st>>>(dd, bo(BK_RAWN + dir), n, stage, dir);
+            mark(BK_RAWN + dir, 1);
+            mark(BK_NORMAL + dir, 0);
+            if (dim == 2) kb_normal<4><<<grid(BK_NORMAL + dir), plan.tpb[BK_NORMAL + dir], 0, st>>>(dd, bo(BK_NORMAL + dir), n, stage, dir);
+            else kb_normal<3><<<grid(BK_NORMAL + dir), plan.tpb[BK_NORMAL + dir], 0, st>>>(dd, bo(BK_NORMAL + dir), n, stage, dir);
+            mark(BK_NORMAL + dir, 1);
+            mark(BK_NAO + dir, 0);
+            if (dim == 2) kb_normal_ao<4><<<grid(BK_NAO + dir), plan.tpb[BK_NAO + dir], 0, st>>>(dd, bo(BK_NAO + dir), n, stage, dir);
+            else kb_normal_ao<3><<<grid(BK_NAO + dir), plan.tpb[BK_NAO + dir], 0, st>>>(dd, bo(BK_NAO + dir), n, stage, dir);
+            mark(BK_NAO + dir, 1);
+            if (dim == 2) {
+                mark(BK_RAWT + dir, 0);
+                kb_raw_tflags<<<grid(BK_RAWT + dir), plan.tpb[BK_RAWT + dir], 0, st>>>(dd, bo(BK_RAWT + dir), n, dir);
+                mark(BK_RAWT + dir, 1);
+                mark(BK_TANG + dir, 0);
+                kb_tang<<<grid(BK_TANG + dir), plan.tpb[BK_TANG + dir], 0, st>>>(dd, bo(BK_TANG + dir), n, stage, dir);
+                mark(BK_TANG + dir, 1);
+                mark(BK_TAO + dir, 0);
+                kb_tang_ao<<<grid(BK_TAO + dir), plan.tpb[BK_TAO + dir], 0, st>>>(dd, bo(BK_TAO + dir), n, stage, dir);
+                mark(BK_TAO + dir, 1);
+            }
+            mark(BK_FLUX + dir, 0);
+            const int tf = plan.tpb[BK_FLUX + dir];
+            if (dim == 2) {
+                if (stage == 0) kb_flux<2, 0><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
+                else kb_flux<2, 1><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
+            } else {
+                if (stage == 0) kb_flux<1, 0><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
+                else kb_flux<1, 1><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
+            }
+            mark(BK_FLUX + dir, 1);
+        }
+        mark(BK_UPD, 0);
+        const int tu = plan.tpb[BK_UPD];
+        if (dim == 2) {
+            if (stage == 0) kb_update<2, 0><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
+            else kb_update<2, 1><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
+        } else {
+            if (stage == 0) kb_update<1, 0><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
+            else kb_update<1, 1><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
+        }
+        mark(BK_UPD, 1);
+    }
+    kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 3, dtend);
     return cudaGetLastError();
 }
 

@@ -32,8 +32,11 @@ EXPORTED = [
     "hgks_config_default", "hgks_create_solver", "hgks_destroy_solver", "hgks_set_state", "hgks_step",
     "hgks_get_state", "hgks_get_time", "hgks_get_stats", "hgks_set_flag_capture", "hgks_flags_size",
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
-    "hgks_batch_step", "hgks_step_noalloc",
+    "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_info", "hgks_batch_last_error",
+    "hgks_batch_destroy", "hgks_step_noalloc",
 ]
+HGKS_BATCH_GRAPH = 1
+HGKS_BATCH_AUTOTUNE = 2
 
 
 class hgks_config(ctypes.Structure):
@@ -96,7 +99,14 @@ def lib():
         L.hgks_last_error.restype = ctypes.c_char_p
         L.hgks_footprint_bytes.argtypes = [ctypes.POINTER(hgks_config)]
         L.hgks_footprint_bytes.restype = ctypes.c_size_t
-        L.hgks_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, vp]
+        L.hgks_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.hgks_batch_step.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int]
+        L.hgks_batch_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.hgks_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+        L.hgks_batch_last_error.argtypes = [vp]
+        L.hgks_batch_last_error.restype = ctypes.c_char_p
+        L.hgks_batch_destroy.argtypes = [vp]
+        L.hgks_batch_destroy.restype = None
         L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp]
         _lib = L
         return L
@@ -245,14 +255,53 @@ class Solver:
             pass
 
 
-def hgks_batch_step(solvers, t_end, stream=None):
-    n = len(solvers)
-    arr = (ctypes.c_void_p * n)(*[s.handle for s in solvers])
-    te = (ctypes.c_double * n)(*[float(t) for t in t_end])
-    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-    rc = lib().hgks_batch_step(arr, n, te, ctypes.c_void_p(st or 0))
-    if rc != HGKS_OK:
-        raise HGKSError(rc, "batch step failed")
+class Batch:
+    """A group of solvers advanced by shared batched launches (hgks_batch_*)."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (ctypes.c_void_p * n)(*[sv.handle for sv in self.solvers])
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        h = ctypes.c_void_p()
+        rc = lib().hgks_batch_create(arr, n, ctypes.c_void_p(st or 0), ctypes.byref(h))
+        if rc != HGKS_OK:
+            raise HGKSError(rc, lib().hgks_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != HGKS_OK:
+            raise HGKSError(rc, lib().hgks_batch_last_error(self._h).decode())
+
+    def hgks_batch_step(self, t_end=None, nsteps=1, graph=True, autotune=False):
+        te = None
+        if t_end is not None:
+            te = (ctypes.c_double * len(self.solvers))(*[float(t) for t in t_end])
+        flags = (HGKS_BATCH_GRAPH if graph else 0) | (HGKS_BATCH_AUTOTUNE if autotune else 0)
+        self._check(lib().hgks_batch_step(self._h, te, int(nsteps), flags))
+
+    def hgks_batch_sync(self):
+        """Wait for the batch; returns (active, failed) solver counts."""
+        n, f = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(lib().hgks_batch_sync(self._h, ctypes.byref(n), ctypes.byref(f)))
+        return n.value, f.value
+
+    def hgks_batch_info(self):
+        tpb = (ctypes.c_int * 64)()
+        steps = ctypes.c_longlong(0)
+        n = lib().hgks_batch_info(self._h, tpb, 64, ctypes.byref(steps))
+        return list(tpb[:n]), steps.value
+
+    def hgks_batch_destroy(self):
+        if getattr(self, "_h", None):
+            lib().hgks_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.hgks_batch_destroy()
+        except Exception:
+            pass
 
 
 def run(cfg: dict, W, t_end: float, max_steps: int = 1 << 30, t0: float = 0.0):

@@ -264,3 +264,58 @@ def random_smooth_2d(nx, ny, seed=7, amp=0.1, bc="periodic"):
     p = field(1.0)
     cfg = base_config(2, nx, ny, 0.0, 1.0, 0.0, 1.0, bc=[bc] * 4)
     return cfg, np.ascontiguousarray(conservative(rho, u, v, p)), 0.05
+
+
+# ---------------------------------------------------------------- many-solve workloads
+
+BATCH_SEED = 20230412
+SERVE_SEED = 20230413
+
+
+def batched_workload(n_solves=256, seed=BATCH_SEED, lo=64, hi=1024):
+    """Independent four-quadrant Riemann solves with sides drawn log-uniformly in [lo, hi]
+    (numpy PCG64), each with its own seeded quadrant states.  Returns a list of (cfg, W)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_solves))).astype(int)
+    out = []
+    for k, n in enumerate(sides):
+        cfg, W, _ = riemann4_2d(int(n), seed=seed + 1 + k)
+        out.append((cfg, W))
+    return out
+
+
+def served_trace(n_requests=1000, rate=200.0, seed=SERVE_SEED, max_1d=8192, max_2d=1024, max_ns=2048):
+    """Poisson-arrival stream of mixed solves: one third each 1D Sod-type shock tubes
+    (256..max_1d cells, log-uniform), 2D Euler four-quadrant Riemann or isentropic-vortex
+    problems (side 64..max_2d), 2D Navier-Stokes viscous shock tubes (nx 128..max_ns,
+    ny = nx/2, Re ~ U[200, 2000]); end times t_end ~ U[0.05, 0.3].  A maximum below its
+    range's lower end lowers that end to it (small traces for tests).
+    Returns a list of dicts {id, arrival, kind, cfg, W, t_end} sorted by arrival time."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo_1d, lo_2d, lo_ns = min(256, max_1d), min(64, max_2d), min(128, max_ns)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        kind = int(rng.integers(0, 3))
+        t_end = float(rng.uniform(0.05, 0.3))
+        if kind == 0:
+            n = int(np.rint(math.exp(rng.uniform(math.log(lo_1d), math.log(max_1d)))))
+            cfg, W, _ = sod_1d(n)
+            name = "sod1d_%d" % n
+        elif kind == 1:
+            n = int(np.rint(math.exp(rng.uniform(math.log(lo_2d), math.log(max_2d)))))
+            if rng.uniform() < 0.5:
+                cfg, W, _ = riemann4_2d(n, seed=seed + 7919 * (i + 1))
+                name = "riemann_%d" % n
+            else:
+                cfg, W, _ = vortex_2d(n)
+                name = "vortex_%d" % n
+        else:
+            nx = int(np.rint(math.exp(rng.uniform(math.log(lo_ns), math.log(max_ns)))))
+            nx += nx % 2
+            Re = float(rng.uniform(200.0, 2000.0))
+            cfg, W, _ = viscous_shock_tube(nx, nx // 2, Re=Re)
+            name = "ns_%dx%d_Re%.0f" % (nx, nx // 2, Re)
+        out.append(dict(id=i, arrival=t, kind=name, cfg=cfg, W=W, t_end=t_end))
+    return out

@@ -1,0 +1,126 @@
+"""Batched execution: solvers of uneven size advanced together by shared launches
+(hgks_batch_*) must produce exactly the bits each produces when stepped alone,
+with or without graph replay and block-size autotuning, and each solver must stop
+at its own end time."""
+import numpy as np
+import pytest
+
+from paper_2304_05572_gb300 import hgks, problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2304_05572_gb300 import _build
+    _build.build()
+
+
+def _cases_2d():
+    out = []
+    for k, (nx, ny) in enumerate([(16, 16), (37, 29), (64, 64), (23, 71), (48, 20)]):
+        cfg, W, _ = P.riemann4_2d(nx, ny=ny, seed=20230412 + k)
+        out.append((cfg, W))
+    cfg, W, _ = P.vortex_2d(32)
+    out.append((cfg, W))
+    cfg, W, _ = P.viscous_shock_tube(40, 20, Re=300.0)
+    out.append((cfg, W))
+    return out
+
+
+def _alone(cfg, W, t_end, steps):
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(np.ascontiguousarray(W))
+    s.hgks_step(t_end, steps, wait=False)     # a latched non-physical state shows in the stats
+    st = s.hgks_get_stats()
+    out, t, n = s.hgks_get_state(), st["t"], st["steps"]
+    s.hgks_destroy_solver()
+    return out, t, n
+
+
+@pytest.mark.parametrize("graph,autotune", [(False, False), (True, False), (True, True)])
+def test_batch_2d_bitwise_equal_to_alone(graph, autotune):
+    import torch
+    cases = _cases_2d()
+    t_end = [0.004 * (1 + k) for k in range(len(cases))]
+    steps = 9
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cfg, W in cases:
+        s = hgks.Solver(cfg, stream=stream)
+        s.hgks_set_state(np.ascontiguousarray(W))
+        solvers.append(s)
+    b = hgks.Batch(solvers, stream=stream)
+    b.hgks_batch_step(t_end, nsteps=steps, graph=graph, autotune=autotune)
+    active, failed = b.hgks_batch_sync()
+    assert failed == 0
+    for k, ((cfg, W), s) in enumerate(zip(cases, solvers)):
+        ref, t_ref, n_ref = _alone(cfg, W, t_end[k], steps)
+        got = s.hgks_get_state()
+        assert np.array_equal(got, ref), k
+        assert s.hgks_get_time() == t_ref
+        assert s.hgks_get_stats()["steps"] == n_ref
+    assert active == sum(1 for k, (cfg, W) in enumerate(cases)
+                         if t_end[k] - solvers[k].hgks_get_time() > 1e-12)
+    tpb, nst = b.hgks_batch_info()
+    assert nst == steps and all(t in (32, 64, 128, 256, 512) for t in tpb)
+    b.hgks_batch_destroy()
+
+
+def test_batch_1d_and_continuation():
+    import torch
+    cases = [P.sod_1d(n)[:2] for n in (50, 200, 333)] + [P.blast_1d(120)[:2]]
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cfg, W in cases:
+        s = hgks.Solver(cfg, stream=stream)
+        s.hgks_set_state(np.ascontiguousarray(W))
+        solvers.append(s)
+    b = hgks.Batch(solvers, stream=stream)
+    t_end = [0.05, 0.02, 0.2, 0.01]
+    for _ in range(4):                    # several calls continue where the last stopped
+        b.hgks_batch_step(t_end, nsteps=5, graph=True)
+    b.hgks_batch_sync()
+    for k, ((cfg, W), s) in enumerate(zip(cases, solvers)):
+        ref, t_ref, n_ref = _alone(cfg, W, t_end[k], 20)
+        assert np.array_equal(s.hgks_get_state(), ref), k
+        assert s.hgks_get_time() == t_ref
+    b.hgks_batch_destroy()
+
+
+def test_batch_rejects_mixed_dimensions():
+    c1, W1, _ = P.sod_1d(40)
+    c2, W2, _ = P.riemann4_2d(16)
+    s1, s2 = hgks.Solver(c1), hgks.Solver(c2)
+    with pytest.raises(hgks.HGKSError) as e:
+        hgks.Batch([s1, s2])
+    assert e.value.code == hgks.HGKS_EINVAL
+
+
+def test_failed_solver_stops_alone_and_others_continue():
+    """A four-quadrant case whose state turns non-physical within a few steps (the scheme
+    has no positivity limiter; the oracle stops on it too) stops at the same step and with
+    the same bits in a batch as alone, and does not stop the other solvers."""
+    import torch
+    bad = P.riemann4_2d(32, seed=P.BATCH_SEED + 1 + 3)[:2]
+    good = [P.riemann4_2d(n, seed=P.BATCH_SEED + 1 + k)[:2] for k, n in ((0, 24), (1, 40))]
+    cases = [good[0], bad, good[1]]
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cfg, W in cases:
+        s = hgks.Solver(cfg, stream=stream)
+        s.hgks_set_state(np.ascontiguousarray(W))
+        solvers.append(s)
+    b = hgks.Batch(solvers, stream=stream)
+    b.hgks_batch_step([1e9] * 3, nsteps=12, graph=True)
+    active, failed = b.hgks_batch_sync()
+    assert failed == 1 and active == 2
+    for (cfg, W), s in zip(cases, solvers):
+        ref, t_ref, n_ref = _alone(cfg, W, 1e9, 12)
+        st = s.hgks_get_stats()
+        assert st["steps"] == n_ref and st["t"] == t_ref
+        assert np.array_equal(s.hgks_get_state(), ref, equal_nan=True)
+    assert solvers[1].hgks_get_stats()["status"] == hgks.HGKS_ENONPHYSICAL
+    assert solvers[1].hgks_get_stats()["steps"] < 12
+    assert solvers[0].hgks_get_stats()["steps"] == 12 and solvers[2].hgks_get_stats()["steps"] == 12
+    b.hgks_batch_destroy()
