@@ -50,6 +50,22 @@ FLUX_DRAM_BYTES_PER_GP = (111.0e6 + 106.0e6) / 2 / (2 * 512 * 513)
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, cells, steps, seconds):
+    """Whole-job Mcell-stage/s of `world` independent replicas, each advancing `cells` cells
+    by `steps` two-stage steps, timed by the slowest rank (`seconds`)."""
+    return world * cells * 2 * steps / seconds / 1e6
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -128,7 +144,7 @@ def run_reference(args, rank, world):
     """Reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
     if rank != 0:
         return 0
-    n_side = 256
+    n_side = args.ref_side
     cores = None
     for _ in range(args.warmup):
         cpu_oracle_rate(n_side, 1)
@@ -137,8 +153,7 @@ def run_reference(args, rank, world):
         _, _, cores = cpu_oracle_rate(n_side, 1)
     dt = time.perf_counter() - t0
     value = n_side * n_side * 2 * args.steps / dt / 1e6
-    sample = "%d S2O4 steps of the same problem at %d^2 cells (1/16 of the 1024^2 grid; per-cell work unchanged)" % (
-        args.steps, n_side)
+    sample = "%d S2O4 steps of the same problem at %d^2 cells (per-cell work as at 1024^2)" % (args.steps, n_side)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -260,6 +275,70 @@ def bench_served(args, torch, hgks, P):
     print(json.dumps(line), flush=True)
 
 
+RECON_CLASSES = ("raw_normal_flags", "normal_recon", "normal_weno_ao", "raw_tangential_flags", "tangential_recon",
+                 "tangential_weno_ao")
+
+# Reconstruction CPU times of the paper (i5-9400, seconds; hybrid, WENO-AO), Tables 3 and 6.
+PAPER_RECON_S = {"sod_100": (0.016, 0.049), "shu_osher_400": (0.245, 1.937), "blast_400": (0.773, 3.176),
+                 "riemann_config1_500": (706.471, 6100.513), "riemann_config6_500": (5546.881, 9628.309),
+                 "double_mach_960x240": (5334.322, 13596.93), "viscous_tube_500x250_Re200": (12148.766, 46394.377)}
+
+
+def bench_recon_cost(args, torch, hgks, P):
+    """Reconstruction cost of the hybrid scheme against WENO-AO everywhere on the paper's
+    test problems (Tables 3 and 6): each problem runs to its end time in both modes with
+    per-kernel-class CUDA events; the reconstruction time is the sum of the indicator and
+    reconstruction classes (normal and tangential), the rest is flux, update, dt, ghosts."""
+    cases = [("sod_100", P.sod_1d(100)), ("shu_osher_400", P.shu_osher_1d(400)), ("blast_400", P.blast_1d(400)),
+             ("riemann_config1_500", P.riemann_config1(500)), ("riemann_config6_500", P.riemann_config6(500)),
+             ("double_mach_960x240", P.double_mach(960, 240)),
+             ("viscous_tube_500x250_Re200", P.viscous_shock_tube(500, 250, Re=200.0))]
+    if args.recon_cases:
+        keep = set(args.recon_cases.split(","))
+        cases = [c for c in cases if c[0] in keep]
+    stream = torch.cuda.Stream()
+    rows = []
+    for name, (cfg, W, t_end) in cases:
+        res = {}
+        for mode in ("hybrid", "wenoao"):
+            s = hgks.Solver(dict(cfg, recon_mode=mode), stream=stream)
+            s.hgks_set_state(np.ascontiguousarray(W))
+            s.hgks_step(t_end, 2, wait=True)           # loads the kernels; not timed
+            s.hgks_set_state(np.ascontiguousarray(W))
+            s.hgks_set_timing(True)
+            steps, status = 0, 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while True:
+                try:
+                    n = s.hgks_step(t_end, 200)
+                except hgks.HGKSError as e:
+                    status = e.code
+                    break
+                steps += n
+                s.hgks_get_timing()                     # recycles the event pairs
+                if n < 200:
+                    break
+            wall = time.perf_counter() - t0
+            tim = s.hgks_get_timing()
+            st = s.hgks_get_stats()
+            s.hgks_destroy_solver()
+            recon = sum(tim[c][0] for c in RECON_CLASSES if c in tim)
+            total = sum(v[0] for v in tim.values())
+            troubled = float(st["troubled"].sum()) / max(1, int(st["examined"].sum()))
+            res[mode] = dict(recon_ms=recon, kernel_ms=total, wall_s=wall, steps=int(st["steps"]),
+                             t=st["t"], status=int(st["status"]), troubled_fraction=troubled)
+        paper = PAPER_RECON_S.get(name)
+        rows.append(dict(case=name, cells=int(np.prod(W.shape[1:])), hybrid=res["hybrid"], wenoao=res["wenoao"],
+                         recon_ratio=res["hybrid"]["recon_ms"] / max(1e-9, res["wenoao"]["recon_ms"]),
+                         total_ratio=res["hybrid"]["kernel_ms"] / max(1e-9, res["wenoao"]["kernel_ms"]),
+                         paper_recon_ratio=paper[0] / paper[1] if paper else None))
+    line = {"metric": "reconstruction time, hybrid WENO-AO / WENO-AO everywhere (GPU kernel time, FP64)",
+            "workload": "the paper's test problems to their end times (Tables 3 and 6)", "cases": rows,
+            "dtype": "f64", "data": "synthetic", "higher_is_better": False}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,7 +347,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE)
-    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served"])
+    ap.add_argument("--ref-side", type=int, default=256, help="grid side of the oracle's bounded sample")
+    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost"])
+    ap.add_argument("--recon-cases", default="", help="comma-separated subset of the recon_cost cases")
     ap.add_argument("--solves", type=int, default=256)
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -304,6 +385,8 @@ def main():
         return bench_batched(args, torch, hgks, P)
     if args.workload == "served":
         return bench_served(args, torch, hgks, P)
+    if args.workload == "recon_cost":
+        return bench_recon_cost(args, torch, hgks, P)
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
@@ -349,12 +432,9 @@ def main():
     stats = solver.hgks_get_stats()
     if stats["status"] != 0:
         raise SystemExit("solver reported status %d" % stats["status"])
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     steps_timed = args.steps
-    value = world * cells * 2 * steps_timed / (ms * 1e-3) / 1e6
+    value = replica_throughput(world, cells, steps_timed, ms * 1e-3)
     troubled = stats["troubled"].sum() / max(1, stats["examined"].sum())
 
     # ---- end-to-end through the C ABI: pinned host state in, one step, pinned host state out
@@ -369,11 +449,8 @@ def main():
         solver.hgks_get_state(Wout)              # D2H of the result (waits for the stream)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * cells * 2 * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_value = replica_throughput(world, cells, e2e_steps, e2e_s)
     state_bytes = int(W0.nbytes)
 
     # ---- dominant kernel roofline (FP64 ALU)

@@ -41,8 +41,17 @@ extern "C" {
 #define HGKS_ETIMEOUT (-4)       /* a bounded device wait ran out */
 #define HGKS_ECUDA (-5)          /* a CUDA runtime call failed */
 
-/* boundary conditions (Sec. 3: periodic, non-reflecting, reflecting, symmetric, no-slip adiabatic) */
-enum { HGKS_BC_PERIODIC = 0, HGKS_BC_EXTRAP = 1, HGKS_BC_REFLECT = 2, HGKS_BC_SYMMETRY = 3, HGKS_BC_NOSLIP = 4 };
+/* boundary conditions (Sec. 3: periodic, non-reflecting, reflecting, symmetric, no-slip adiabatic;
+ * Sec. 3.5, double Mach reflection: a prescribed inflow state, a wall that starts at x = shock_x0
+ * with the inflow state ahead of it, and a top boundary that follows the exact motion of the
+ * oblique shock).  All ghost values are set at the ghost cell's centre (x_c, y_c), at the time of
+ * the stage being evaluated (t^n for the first stage, t^n + dt/2 for the second):
+ *   HGKS_BC_INFLOW:      ghost = bc_state[side]
+ *   HGKS_BC_SHOCK_WALL:  (y-lo, 2D) x_c < shock_x0: bc_state[side]; else reflecting
+ *   HGKS_BC_SHOCK_TRACK: (y-lo or y-hi, 2D) x_c < shock_x0 + shock_cot (y_c + shock_speed t):
+ *                        bc_state[side] (behind the shock); else shock_pre (ahead of it) */
+enum { HGKS_BC_PERIODIC = 0, HGKS_BC_EXTRAP = 1, HGKS_BC_REFLECT = 2, HGKS_BC_SYMMETRY = 3, HGKS_BC_NOSLIP = 4,
+       HGKS_BC_INFLOW = 5, HGKS_BC_SHOCK_WALL = 6, HGKS_BC_SHOCK_TRACK = 7 };
 /* reconstruction: hybrid (the paper's method), linear upwind only, WENO-AO everywhere (Sec. 3, Tables 1 and 4) */
 enum { HGKS_RECON_HYBRID = 0, HGKS_RECON_LINEAR = 1, HGKS_RECON_WENOAO = 2 };
 /* readings of zeta1 = "5/17 dx" in Step 1 (Sec. 2.3.1): A = (5/17) dx, B = 5/(17 dx) (default), C = 5/17 in cell units */
@@ -64,6 +73,9 @@ typedef struct hgks_config {
     int zeta1_mode;           /* HGKS_ZETA1_* */
     double gamma_hi, gamma_lo;/* WENO-AO linear weights, Eq. (35) (0.85, 0.85) */
     double eps;               /* WENO-AO epsilon, Eq. (37) (1e-8) */
+    double bc_state[4][4];    /* conservative state [side][component] for HGKS_BC_INFLOW / _SHOCK_* sides */
+    double shock_pre[4];      /* conservative state ahead of the shock (HGKS_BC_SHOCK_TRACK) */
+    double shock_x0, shock_cot, shock_speed;   /* shock line x = shock_x0 + shock_cot (y + shock_speed t) */
 } hgks_config;
 
 typedef struct hgks_stats {
@@ -212,7 +224,8 @@ void hgks_batch_destroy(hgks_batch* b);
  * device-wide synchronisation cudaMalloc/cudaFree may cause.  The paper has no
  * counterpart; the arithmetic is exactly that of hgks_step on a solver created
  * from *cfg (same kernels, dt from the CFL rule or cfg->fixed_dt, no t_end
- * clipping).
+ * clipping).  The step starts at t = 0: boundaries that move with time
+ * (HGKS_BC_SHOCK_TRACK) take their t = 0 position.
  *
  * W_in, W_out: device memory of the current device, [nv][ny][nx] FP64 as
  * everywhere in this ABI, owned by the caller; they may be the same buffer.

@@ -28,7 +28,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libhgks_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "extrap": 1, "reflect": 2, "symmetry": 3, "noslip": 4}
+BC = {"periodic": 0, "extrap": 1, "reflect": 2, "symmetry": 3, "noslip": 4, "inflow": 5, "shock_wall": 6,
+      "shock_track": 7}
 RECON = {"hybrid": 0, "linear": 1, "wenoao": 2}
 ZETA1 = {"A": 0, "B": 1, "C": 2}
 NG = 4
@@ -63,6 +64,9 @@ class Config(ctypes.Structure):
         ("zeta1_mode", ctypes.c_int),
         ("gamma_hi", ctypes.c_double), ("gamma_lo", ctypes.c_double), ("eps", ctypes.c_double),
         ("threads", ctypes.c_int),
+        ("bc_state", (ctypes.c_double * 4) * 4),
+        ("shock_pre", ctypes.c_double * 4),
+        ("shock_x0", ctypes.c_double), ("shock_cot", ctypes.c_double), ("shock_speed", ctypes.c_double),
     ]
 
 
@@ -78,7 +82,7 @@ def lib():
             L = ctypes.CDLL(path)
             L.or_run.argtypes = [ctypes.POINTER(Config), _DP, _DP, ctypes.c_double, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_int), _DP]
-            L.or_step_flags.argtypes = [ctypes.POINTER(Config), _DP, ctypes.c_double, _DP,
+            L.or_step_flags.argtypes = [ctypes.POINTER(Config), _DP, ctypes.c_double, ctypes.c_double, _DP,
                                         ctypes.POINTER(_U8P), ctypes.POINTER(_DP), _DP]
             L.or_cfl_dt.argtypes = [ctypes.POINTER(Config), _DP]
             L.or_cfl_dt.restype = ctypes.c_double
@@ -105,7 +109,7 @@ def lib():
             L.or_weno_ao_face.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _DP, _DP, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, _DP, _DP]
-            L.or_fill_ghosts.argtypes = [ctypes.POINTER(Config), _DP, _DP]
+            L.or_fill_ghosts.argtypes = [ctypes.POINTER(Config), _DP, ctypes.c_double, _DP]
             L.or_threads_used.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
@@ -144,6 +148,15 @@ def make_config(cfg: dict, threads: int = 0) -> Config:
     c.gamma_hi = float(cfg.get("gamma_hi", 0.85)); c.gamma_lo = float(cfg.get("gamma_lo", 0.85))
     c.eps = float(cfg.get("eps", 1e-8))
     c.threads = int(threads)
+    for k, st in enumerate(cfg.get("bc_state", [None] * 4)):
+        if st is not None:
+            for j, v in enumerate(st):
+                c.bc_state[k][j] = float(v)
+    for j, v in enumerate(cfg.get("shock_pre", [])):
+        c.shock_pre[j] = float(v)
+    c.shock_x0 = float(cfg.get("shock_x0", 0.0))
+    c.shock_cot = float(cfg.get("shock_cot", 0.0))
+    c.shock_speed = float(cfg.get("shock_speed", 0.0))
     return c
 
 
@@ -180,8 +193,8 @@ def flag_shapes(cfg: dict):
 
 
 def step_flags(cfg: dict, W: np.ndarray, dt: float = 0.0, threads: int = 0, margins: bool = False,
-               wstar: np.ndarray = None):
-    """One S2O4 step; returns (W_next, dt_used, flags) with flags[(stage, dir, kind)] arrays,
+               wstar: np.ndarray = None, t0: float = 0.0):
+    """One S2O4 step from time t0; returns (W_next, dt_used, flags) with flags[(stage, dir, kind)] arrays,
     and with margins=True also the relative decision margins in the same layout.  If wstar
     (same shape as W) is given it receives the first-stage state W*."""
     c = make_config(cfg, threads)
@@ -202,7 +215,7 @@ def step_flags(cfg: dict, W: np.ndarray, dt: float = 0.0, threads: int = 0, marg
                         mbufs[(s, d, kind)] = mb
                         mptrs[(s * 2 + d) * 2 + ki] = mb.ctypes.data_as(_DP)
     dtu = ctypes.c_double(0.0)
-    st = lib().or_step_flags(ctypes.byref(c), _dp(Wc), float(dt), ctypes.byref(dtu), ptrs,
+    st = lib().or_step_flags(ctypes.byref(c), _dp(Wc), float(t0), float(dt), ctypes.byref(dtu), ptrs,
                              mptrs if margins else None, _dp(wstar) if wstar is not None else None)
     _check(st, "step")
     if margins:
@@ -318,12 +331,12 @@ def weno_ao_face(dim, gamma, Qw, Qs, nx, ny, side, ghi=0.85, glo=0.85, eps=1e-8)
     return v[: dim + 2], d[: dim + 2]
 
 
-def fill_ghosts(cfg, W):
+def fill_ghosts(cfg, W, t=0.0):
     c = make_config(cfg)
     dim, nx, ny = int(cfg["dim"]), int(cfg["nx"]), int(cfg.get("ny", 1))
     nv = dim + 2
     NY = ny + 2 * NG if dim == 2 else 1
     out = np.zeros((nv, NY, nx + 2 * NG))
     Wc = np.ascontiguousarray(W, dtype=np.float64)
-    _check(lib().or_fill_ghosts(ctypes.byref(c), _dp(Wc), _dp(out)), "fill_ghosts")
+    _check(lib().or_fill_ghosts(ctypes.byref(c), _dp(Wc), float(t), _dp(out)), "fill_ghosts")
     return out

@@ -37,7 +37,8 @@
 #define MAXT 160    /* terms of a polynomial in (u, v, xi^2) */
 #define NMOM 10     /* highest velocity power needed is u^7 (flux of the slope term) */
 
-enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4 };
+enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4,
+       BC_INFLOW = 5, BC_SHOCK_WALL = 6, BC_SHOCK_TRACK = 7 };
 enum { RECON_HYBRID = 0, RECON_LINEAR = 1, RECON_WENOAO = 2 };
 enum { ZETA1_A = 0, ZETA1_B = 1, ZETA1_C = 2 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ENONPHYSICAL = -3 };
@@ -56,6 +57,10 @@ typedef struct {
     int zeta1_mode;
     double gamma_hi, gamma_lo, eps;
     int threads;
+    /* prescribed boundaries of the double Mach reflection problem (Sec. 3.5) */
+    double bc_state[4][4];   /* conservative state per side (inflow; behind the shock) */
+    double shock_pre[4];     /* conservative state ahead of the shock */
+    double shock_x0, shock_cot, shock_speed;   /* shock line x = shock_x0 + shock_cot (y + shock_speed t) */
 } or_config;
 
 /* ------------------------------------------------------------------------ */
@@ -751,13 +756,33 @@ static inline size_t pidx(const grid* g, int k, int j, int i)
 /* Ghost fill: x ghosts on the interior rows, then y ghosts over the full padded
  * width (this fills the corners).  Reading: non-reflecting = zero-gradient copy
  * of the boundary cell; reflecting / symmetric = mirror with the normal
- * momentum negated; no-slip adiabatic = mirror with both momenta negated. */
-static void ghost_value(const grid* g, const double* Wp, int bc, int axis, int k, int j, int i,
-                        int src_j, int src_i, int mirror_j, int mirror_i, double* out)
+ * momentum negated; no-slip adiabatic = mirror with both momenta negated.
+ * Double Mach reflection (Sec. 3.5): the post-shock state flows in on the left
+ * and on the bottom up to x = 1/6, the bottom is a slip wall from there on, and
+ * the top follows the exact motion of the oblique Mach 10 shock.  Reading: each
+ * ghost cell takes the state at its centre (x_c, y_c) at the time of the stage
+ * (t^n in the first stage, t^n + dt/2 = t* in the second), the post-shock state
+ * where x_c lies behind the shock line x = 1/6 + cot(60 deg) (y + 20 t), the
+ * pre-shock state elsewhere.  (The shock moves at 10 along its normal, so its
+ * trace on a horizontal line moves at 10 / sin 60 deg = cot 60 deg x 20.)  The
+ * line's data are configuration values (shock_x0, shock_cot, shock_speed). */
+static double cell_centre(double origin, int i, double h) { return origin + ((double)i + 0.5) * h; }
+
+static void ghost_value(const grid* g, const double* Wp, int bc, int axis, int side, int k, int j, int i,
+                        int src_j, int src_i, int mirror_j, int mirror_i, double t, double* out)
 {
-    (void)j; (void)i;
     int nv = g->nv;
+    const or_config* c = &g->c;
+    int sidx = 2 * axis + side;
     double v;
+    if (bc == BC_INFLOW) { *out = c->bc_state[sidx][k]; return; }
+    if (bc == BC_SHOCK_TRACK) {
+        double xc = cell_centre(c->x0, i, g->dx), yc = cell_centre(c->y0, j, g->dy);
+        double xs = c->shock_x0 + c->shock_cot * (yc + c->shock_speed * t);
+        *out = xc < xs ? c->bc_state[sidx][k] : c->shock_pre[k];
+        return;
+    }
+    if (bc == BC_SHOCK_WALL && cell_centre(c->x0, i, g->dx) < c->shock_x0) { *out = c->bc_state[sidx][k]; return; }
     if (bc == BC_PERIODIC || bc == BC_EXTRAP) v = Wp[pidx(g, k, src_j, src_i)];
     else {
         v = Wp[pidx(g, k, mirror_j, mirror_i)];
@@ -768,7 +793,7 @@ static void ghost_value(const grid* g, const double* Wp, int bc, int axis, int k
     *out = v;
 }
 
-static void fill_ghosts(const grid* g, double* Wp)
+static void fill_ghosts(const grid* g, double* Wp, double t)
 {
     int nx = g->c.nx, ny = g->c.ny, nv = g->nv, dim = g->c.dim;
     int jlo = 0, jhi = dim == 2 ? ny : 1;
@@ -779,10 +804,10 @@ static void fill_ghosts(const grid* g, double* Wp)
                 double v;
                 int bl = g->c.bc[0], bh = g->c.bc[1];
                 int srcL = bl == BC_PERIODIC ? nx - l : 0;
-                ghost_value(g, Wp, bl, 0, k, jr, -l, jr, srcL, jr, l - 1, &v);
+                ghost_value(g, Wp, bl, 0, 0, k, jr, -l, jr, srcL, jr, l - 1, t, &v);
                 Wp[pidx(g, k, jr, -l)] = v;
                 int srcH = bh == BC_PERIODIC ? l - 1 : nx - 1;
-                ghost_value(g, Wp, bh, 0, k, jr, nx - 1 + l, jr, srcH, jr, nx - l, &v);
+                ghost_value(g, Wp, bh, 0, 1, k, jr, nx - 1 + l, jr, srcH, jr, nx - l, t, &v);
                 Wp[pidx(g, k, jr, nx - 1 + l)] = v;
             }
     if (dim == 1) return;
@@ -792,10 +817,10 @@ static void fill_ghosts(const grid* g, double* Wp)
                 double v;
                 int bl = g->c.bc[2], bh = g->c.bc[3];
                 int srcL = bl == BC_PERIODIC ? ny - l : 0;
-                ghost_value(g, Wp, bl, 1, k, -l, i, srcL, i, l - 1, i, &v);
+                ghost_value(g, Wp, bl, 1, 0, k, -l, i, srcL, i, l - 1, i, t, &v);
                 Wp[pidx(g, k, -l, i)] = v;
                 int srcH = bh == BC_PERIODIC ? l - 1 : ny - 1;
-                ghost_value(g, Wp, bh, 1, k, ny - 1 + l, i, srcH, i, ny - l, i, &v);
+                ghost_value(g, Wp, bh, 1, 1, k, ny - 1 + l, i, srcH, i, ny - l, i, t, &v);
                 Wp[pidx(g, k, ny - 1 + l, i)] = v;
             }
 }
@@ -1068,7 +1093,7 @@ typedef struct {
 /* One S2O4 step (Sec. 2.2): stage 1 with the dt and dt/2 fluxes at t_n gives
  * F^n, dF^n (Eqs. (17)-(18)) and W* (Eq. (19)); stage 2 at t* gives dF*, then
  * the fluxes of Eqs. (20)-(21) and W^{n+1} (Eq. (22)). */
-static int s2o4_step(const grid* g, double* Wp, double dt, step_flags* sf)
+static int s2o4_step(const grid* g, double* Wp, double t, double dt, step_flags* sf)
 {
     const or_config* c = &g->c;
     int nx = c->nx, ny = c->ny, nv = g->nv, dim = c->dim;
@@ -1091,7 +1116,7 @@ static int s2o4_step(const grid* g, double* Wp, double dt, step_flags* sf)
     memcpy(Wn, Wp, sizeof(double) * npad);
 
     /* ---- stage 1 ---- */
-    fill_ghosts(g, Wn);
+    fill_ghosts(g, Wn, t);
     for (int d = 0; d < ndir && st == OR_OK; d++) {
         flag_out fo = {sf ? sf->flags[0][d][0] : NULL, sf ? sf->flags[0][d][1] : NULL,
                        sf ? sf->margins[0][d][0] : NULL, sf ? sf->margins[0][d][1] : NULL};
@@ -1123,8 +1148,8 @@ static int s2o4_step(const grid* g, double* Wp, double dt, step_flags* sf)
                 for (int i = 0; i < nx; i++)
                     sf->wstar[((size_t)k * (dim == 2 ? ny : 1) + j) * nx + i] = Ws[pidx(g, k, dim == 2 ? j : 0, i)];
 
-    /* ---- stage 2 ---- */
-    fill_ghosts(g, Ws);
+    /* ---- stage 2 (at t* = t^n + dt/2) ---- */
+    fill_ghosts(g, Ws, t + 0.5 * dt);
     for (int d = 0; d < ndir && st == OR_OK; d++) {
         flag_out fo = {sf ? sf->flags[1][d][0] : NULL, sf ? sf->flags[1][d][1] : NULL,
                        sf ? sf->margins[1][d][0] : NULL, sf ? sf->margins[1][d][1] : NULL};
@@ -1211,7 +1236,7 @@ int or_run(const or_config* cfg, double* W, double* t, double t_end, int max_ste
     while (n < max_steps && t_end - *t > tol) {
         double dt = cfl_dt(&g, Wp);
         if (*t + dt > t_end) dt = t_end - *t;
-        st = s2o4_step(&g, Wp, dt, NULL);
+        st = s2o4_step(&g, Wp, *t, dt, NULL);
         if (st != OR_OK) break;
         *t += dt;
         n++;
@@ -1223,9 +1248,9 @@ int or_run(const or_config* cfg, double* W, double* t, double t_end, int max_ste
     return st;
 }
 
-/* One step with flag capture.  dt <= 0 selects the CFL time step.
+/* One step from time t with flag capture.  dt <= 0 selects the CFL time step.
  * flags, margins: arrays of 8 pointers [stage][dir][normal/tangential], each may be NULL. */
-int or_step_flags(const or_config* cfg, double* W, double dt, double* dt_used, uint8_t** flags, double** margins,
+int or_step_flags(const or_config* cfg, double* W, double t, double dt, double* dt_used, uint8_t** flags, double** margins,
                   double* wstar)
 {
     grid g;
@@ -1243,7 +1268,7 @@ int or_step_flags(const or_config* cfg, double* W, double dt, double* dt_used, u
         sf.margins[s][d][k] = margins ? margins[(s * 2 + d) * 2 + k] : NULL;
     }
     sf.wstar = wstar;
-    st = s2o4_step(&g, Wp, dt, &sf);
+    st = s2o4_step(&g, Wp, t, dt, &sf);
     from_padded(&g, Wp, W);
     free(Wp);
     if (dt_used) *dt_used = dt;
@@ -1365,7 +1390,7 @@ void or_weno_ao_face(int dim, double gam, double ghi, double glo, double eps, co
 }
 
 /* Ghost-filled padded state (for the boundary-condition tests). */
-int or_fill_ghosts(const or_config* cfg, const double* W, double* Wpad)
+int or_fill_ghosts(const or_config* cfg, const double* W, double t, double* Wpad)
 {
     grid g;
     int st = grid_setup(cfg, &g);
@@ -1373,7 +1398,7 @@ int or_fill_ghosts(const or_config* cfg, const double* W, double* Wpad)
     size_t npad = (size_t)g.nv * g.NY * g.NX;
     memset(Wpad, 0, sizeof(double) * npad);
     to_padded(&g, W, Wpad);
-    fill_ghosts(&g, Wpad);
+    fill_ghosts(&g, Wpad, t);
     return OR_OK;
 }
 

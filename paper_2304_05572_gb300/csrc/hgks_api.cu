@@ -62,7 +62,21 @@ int validate(const hgks_config* c, char* err)
     if (c->c1 < 0.0 || c->c2 < 0.0) { set_err(err, "c1, c2 must be >= 0"); return HGKS_EINVAL; }
     int nb = c->dim == 2 ? 4 : 2;
     for (int k = 0; k < nb; k++)
-        if (c->bc[k] < HGKS_BC_PERIODIC || c->bc[k] > HGKS_BC_NOSLIP) { set_err(err, "bad boundary type %d", c->bc[k]); return HGKS_EINVAL; }
+        if (c->bc[k] < HGKS_BC_PERIODIC || c->bc[k] > HGKS_BC_SHOCK_TRACK) { set_err(err, "bad boundary type %d", c->bc[k]); return HGKS_EINVAL; }
+    for (int k = 0; k < nb; k++) {
+        if (c->bc[k] == HGKS_BC_SHOCK_WALL && k != 2) { set_err(err, "HGKS_BC_SHOCK_WALL is a y-lo boundary"); return HGKS_EINVAL; }
+        if (c->bc[k] == HGKS_BC_SHOCK_TRACK && k < 2) { set_err(err, "HGKS_BC_SHOCK_TRACK is a y boundary"); return HGKS_EINVAL; }
+        if (c->bc[k] >= HGKS_BC_INFLOW) {
+            bool ok = c->bc_state[k][0] > 0.0;
+            for (int j = 0; j < c->dim + 2; j++) ok = ok && std::isfinite(c->bc_state[k][j]);
+            if (c->bc[k] == HGKS_BC_SHOCK_TRACK) {
+                ok = ok && c->shock_pre[0] > 0.0 && std::isfinite(c->shock_cot) && std::isfinite(c->shock_speed);
+                for (int j = 0; j < c->dim + 2; j++) ok = ok && std::isfinite(c->shock_pre[j]);
+            }
+            if (c->bc[k] >= HGKS_BC_SHOCK_WALL) ok = ok && std::isfinite(c->shock_x0);
+            if (!ok) { set_err(err, "boundary %d needs finite prescribed states with rho > 0 (and shock data)", k); return HGKS_EINVAL; }
+        }
+    }
     for (int a = 0; a < nb; a += 2)
         if ((c->bc[a] == HGKS_BC_PERIODIC) != (c->bc[a + 1] == HGKS_BC_PERIODIC)) {
             set_err(err, "periodic boundaries must be paired on an axis"); return HGKS_EINVAL;
@@ -97,6 +111,11 @@ void fill_params(const hgks_config* c, Params& P)
     P.cfl = c->cfl; P.fixed_dt = c->fixed_dt;
     P.viscous = c->viscous; P.tau_zero = c->tau_zero; P.recon_mode = c->recon_mode;
     for (int k = 0; k < 4; k++) P.bc[k] = c->bc[k];
+    P.x0 = c->x0; P.y0 = c->dim == 2 ? c->y0 : 0.0;
+    for (int k = 0; k < 4; k++)
+        for (int j = 0; j < 4; j++) P.bc_state[k][j] = c->bc_state[k][j];
+    for (int j = 0; j < 4; j++) P.shock_pre[j] = c->shock_pre[j];
+    P.shock_x0 = c->shock_x0; P.shock_cot = c->shock_cot; P.shock_speed = c->shock_speed;
     double ghi = c->gamma_hi, glo = c->gamma_lo;
     P.g_ao[3] = ghi;
     P.g_ao[0] = ((1.0 - ghi) * (1.0 - glo)) * 0.5;

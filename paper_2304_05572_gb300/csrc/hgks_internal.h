@@ -65,6 +65,10 @@ struct Params {
     int viscous, tau_zero, recon_mode;
     int bc[4];
     double g_ao[4], g3inv, gr[3], eps;
+    double x0, y0;                 // domain origin (ghost-cell centres of the prescribed boundaries)
+    double bc_state[4][4];         // prescribed boundary states [side][global component]
+    double shock_pre[4];
+    double shock_x0, shock_cot, shock_speed;
 };
 
 struct TimerRec { int cls; cudaEvent_t a, b; };

@@ -29,7 +29,22 @@ __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
 // ---------------------------------------------------------------- ghost cells
 // x ghosts on interior rows, then y ghosts over the padded width (fills corners).
 // Non-reflecting: zero-gradient copy; reflect / symmetry: mirror, normal momentum negated;
-// no-slip adiabatic: mirror, both momenta negated.
+// no-slip adiabatic: mirror, both momenta negated.  Prescribed states (Sec. 3.5): inflow,
+// the wall that starts at x = shock_x0, and the boundary that follows the oblique shock line
+// x = shock_x0 + shock_cot (y + shock_speed t), all evaluated at the ghost cell's centre at the
+// stage time (t^n, or t^n + dt/2 in the second stage).  The centre and line positions are
+// computed in one fixed IEEE order (no contraction) so that the side of the line a ghost cell
+// falls on is the same in every implementation that follows this order.
+__device__ __forceinline__ double stage_time(const Ctrl* ctrl, int stage)
+{
+    return stage == 0 ? ctrl->t : (ex(ctrl->t) + ex(0.5) * ex(ctrl->dt)).v;
+}
+
+__device__ __forceinline__ double cell_centre(double origin, int i, double h)
+{
+    return (ex(origin) + (ex((double)i) + ex(0.5)) * ex(h)).v;
+}
+
 __device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
@@ -43,12 +58,13 @@ __device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ 
     int k = (int)(id / rowsI);
     int bc = P.bc[side];
     int dst = side == 0 ? -l : g.nx - 1 + l;
+    double* base = W + g.origin + (long long)k * g.plane + (long long)j * g.pitch;
+    if (bc == HGKS_BC_INFLOW) { base[dst] = P.bc_state[side][k]; return; }
     int src;
     bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP;
     if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.nx - l : l - 1;
     else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.nx - 1;
     else src = side == 0 ? l - 1 : g.nx - l;
-    double* base = W + g.origin + (long long)k * g.plane + (long long)j * g.pitch;
     double v = base[src];
     if (mirror) {
         if (k == 1) v = -v;
@@ -63,7 +79,7 @@ __global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restri
 }
 
 
-__device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
+__device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, int stage, long long id)
 {
     if (ctrl->done) return;
     const GridGeom& g = P.g;
@@ -76,12 +92,24 @@ __device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ 
     int k = (int)(id / NG);
     int bc = P.bc[2 + side];
     int dst = side == 0 ? -l : g.ny - 1 + l;
+    double* base = W + g.origin + (long long)k * g.plane + i;
+    if (bc == HGKS_BC_INFLOW) { base[(long long)dst * g.pitch] = P.bc_state[2 + side][k]; return; }
+    if (bc == HGKS_BC_SHOCK_TRACK) {
+        const double xc = cell_centre(P.x0, i, g.dx), yc = cell_centre(P.y0, dst, g.dy);
+        const double t = stage_time(ctrl, stage);
+        const double xs = (ex(P.shock_x0) + ex(P.shock_cot) * (ex(yc) + ex(P.shock_speed) * ex(t))).v;
+        base[(long long)dst * g.pitch] = xc < xs ? P.bc_state[2 + side][k] : P.shock_pre[k];
+        return;
+    }
+    if (bc == HGKS_BC_SHOCK_WALL && cell_centre(P.x0, i, g.dx) < P.shock_x0) {
+        base[(long long)dst * g.pitch] = P.bc_state[2 + side][k];
+        return;
+    }
     int src;
-    bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP;
+    bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP || bc == HGKS_BC_SHOCK_WALL;
     if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.ny - l : l - 1;
     else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.ny - 1;
     else src = side == 0 ? l - 1 : g.ny - l;
-    double* base = W + g.origin + (long long)k * g.plane + i;
     double v = base[(long long)src * g.pitch];
     if (mirror) {
         if (k == 2) v = -v;
@@ -90,9 +118,9 @@ __device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ 
     base[(long long)dst * g.pitch] = v;
 }
 
-__global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, int stage)
 {
-    b_ghost_y(P, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_ghost_y(P, W, ctrl, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -698,7 +726,7 @@ __global__ void kb_ghost(const SolveDesc* __restrict__ D, const int* __restrict_
     HGKS_BATCH_BLOCK();
     double* W = stage == 0 ? d.W : d.Ws;
     if (axis == 0) b_ghost_x(d.P, W, d.ctrl, id);
-    else b_ghost_y(d.P, W, d.ctrl, id);
+    else b_ghost_y(d.P, W, d.ctrl, stage, id);
 }
 
 template <int NV>
@@ -849,7 +877,7 @@ static void enqueue_stage(hgks_solver* s, int stage)
     timed(s, KC_GHOST, DIM == 2 ? 2 : 1, [&] {
         int rowsI = DIM == 2 ? P.g.ny : 1;
         k_ghost_x<<<blocks_for((long long)P.g.nv * rowsI * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
-        if (DIM == 2) k_ghost_y<<<blocks_for((long long)P.g.nv * (P.g.nx + 2 * NG) * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
+        if (DIM == 2) k_ghost_y<<<blocks_for((long long)P.g.nv * (P.g.nx + 2 * NG) * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl, stage);
     });
     enqueue_sweep<DIM>(s, 0, stage, Win);
     if (DIM == 2) enqueue_sweep<DIM>(s, 1, stage, Win);

@@ -24,7 +24,8 @@ HGKS_ETIMEOUT = -4
 HGKS_ECUDA = -5
 ERR_NAMES = {-1: "HGKS_EINVAL", -2: "HGKS_ENOMEM", -3: "HGKS_ENONPHYSICAL", -4: "HGKS_ETIMEOUT", -5: "HGKS_ECUDA"}
 
-BC = {"periodic": 0, "extrap": 1, "reflect": 2, "symmetry": 3, "noslip": 4}
+BC = {"periodic": 0, "extrap": 1, "reflect": 2, "symmetry": 3, "noslip": 4, "inflow": 5, "shock_wall": 6,
+      "shock_track": 7}
 RECON = {"hybrid": 0, "linear": 1, "wenoao": 2}
 ZETA1 = {"A": 0, "B": 1, "C": 2}
 
@@ -52,6 +53,9 @@ class hgks_config(ctypes.Structure):
         ("bc", ctypes.c_int * 4),
         ("recon_mode", ctypes.c_int), ("zeta1_mode", ctypes.c_int),
         ("gamma_hi", ctypes.c_double), ("gamma_lo", ctypes.c_double), ("eps", ctypes.c_double),
+        ("bc_state", (ctypes.c_double * 4) * 4),
+        ("shock_pre", ctypes.c_double * 4),
+        ("shock_x0", ctypes.c_double), ("shock_cot", ctypes.c_double), ("shock_speed", ctypes.c_double),
     ]
 
 
@@ -141,6 +145,15 @@ def make_config(cfg: dict) -> hgks_config:
     zm = cfg.get("zeta1_mode")
     if zm is not None:
         c.zeta1_mode = ZETA1[zm] if isinstance(zm, str) else int(zm)
+    for k, st in enumerate(cfg.get("bc_state", [None] * 4)):
+        if st is not None:
+            for j, v in enumerate(st):
+                c.bc_state[k][j] = float(v)
+    for j, v in enumerate(cfg.get("shock_pre", [])):
+        c.shock_pre[j] = float(v)
+    for key in ("shock_x0", "shock_cot", "shock_speed"):
+        if key in cfg:
+            setattr(c, key, float(cfg[key]))
     return c
 
 

@@ -238,6 +238,64 @@ def viscous_shock_tube(nx=500, ny=None, Re=200.0, prandtl=1.0, cfl=0.3):
     return cfg, W, 1.0
 
 
+# ---- double Mach reflection (Sec. 3.5)
+DMR_POST = (8.0, 4.125 * math.sqrt(3.0), -4.125, 116.5)     # (rho, U, V, p) behind the Mach 10 shock
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)                               # ahead of it
+DMR_X0 = 1.0 / 6.0                                           # the shock meets the wall at x = 1/6 at t = 0
+DMR_COT = 1.0 / math.sqrt(3.0)                               # cot 60 deg: the shock is inclined 60 deg to the x-axis
+DMR_SPEED = 20.0                                             # line x = 1/6 + (y + 20 t)/sqrt(3) (normal speed 10)
+
+
+def _halfplane_fraction(xe, ye, a, c):
+    """Exact area fraction of each cell [xe_i, xe_i+1] x [ye_j, ye_j+1] lying in x < a + c y (c > 0)."""
+    xl, xr = xe[None, :-1], xe[None, 1:]
+    yl, yr = ye[:-1, None], ye[1:, None]
+    dx = xr - xl
+
+    def ramp_integral(z):              # int_{-inf}^{z} clip(s, 0, dx) ds
+        return np.where(z <= 0.0, 0.0, np.where(z <= dx, 0.5 * z * z, 0.5 * dx * dx + dx * (z - dx)))
+
+    area = (ramp_integral(a + c * yr - xl) - ramp_integral(a + c * yl - xl)) / c
+    return np.clip(area / (dx * (yr - yl)), 0.0, 1.0)
+
+
+def _oblique_shock_state(nx, ny, x0, x1, y0, y1, t=0.0):
+    """Exact cell averages of the straight Mach 10 shock of Sec. 3.5 at time t (no wall)."""
+    frac = _halfplane_fraction(_edges(x0, x1, nx), _edges(y0, y1, ny), DMR_X0 + DMR_COT * DMR_SPEED * t, DMR_COT)
+    post, pre = conservative(*DMR_POST), conservative(*DMR_PRE)
+    return np.ascontiguousarray(frac[None] * post[:, None, None] + (1.0 - frac[None]) * pre[:, None, None])
+
+
+def double_mach(nx=960, ny=240, cfl=0.8):
+    """Sec. 3.5: [0, 4] x [0, 1], the Mach 10 shock at 60 deg through (1/6, 0), the post-shock
+    state flowing in on the left and on the bottom up to x = 1/6, a slip wall beyond, the top
+    following the exact shock motion, the right end non-reflecting; c1 = 0, c2 = 1, t = 0.2."""
+    post = conservative(*DMR_POST)
+    cfg = base_config(2, nx, ny, 0.0, 4.0, 0.0, 1.0, cfl=cfl, c1=0.0, c2=1.0,
+                      bc=["inflow", "extrap", "shock_wall", "shock_track"],
+                      bc_state=[list(post), [0.0] * 4, list(post), list(post)],
+                      shock_pre=list(conservative(*DMR_PRE)), shock_x0=DMR_X0, shock_cot=DMR_COT,
+                      shock_speed=DMR_SPEED)
+    return cfg, _oblique_shock_state(nx, ny, 0.0, 4.0, 0.0, 1.0), 0.2
+
+
+def oblique_shock(nx=64, ny=32, cfl=0.8, x1=1.0, y1=0.5):
+    """The straight Mach 10 shock of Sec. 3.5 alone (no wall): post-shock inflow on the left,
+    both y-sides following the exact shock motion, non-reflecting right end.  Its exact
+    solution is the initial discontinuity translated at the shock speed."""
+    post = conservative(*DMR_POST)
+    cfg = base_config(2, nx, ny, 0.0, x1, 0.0, y1, cfl=cfl, c1=0.0, c2=1.0,
+                      bc=["inflow", "extrap", "shock_track", "shock_track"],
+                      bc_state=[list(post), [0.0] * 4, list(post), list(post)],
+                      shock_pre=list(conservative(*DMR_PRE)), shock_x0=DMR_X0, shock_cot=DMR_COT,
+                      shock_speed=DMR_SPEED)
+    return cfg, _oblique_shock_state(nx, ny, 0.0, x1, 0.0, y1)
+
+
+def oblique_shock_exact(nx, ny, t, x1=1.0, y1=0.5):
+    return _oblique_shock_state(nx, ny, 0.0, x1, 0.0, y1, t)
+
+
 def uniform_2d(n, state=(1.3, 0.4, -0.7, 2.1), bc="periodic", ny=None):
     ny = n if ny is None else ny
     cfg = base_config(2, n, ny, 0.0, 1.0, 0.0, 1.0, bc=[bc] * 4)

@@ -50,7 +50,7 @@ def gpu_step(cfg, W, t0=0.0, dt=None):
     return out, st, flags
 
 
-def check_step(cfg, W, label=""):
+def check_step(cfg, W, label="", t0=0.0):
     """One step from the same state on both sides.
 
     * dt and the first-stage flags (computed from identical inputs) must be identical;
@@ -61,9 +61,9 @@ def check_step(cfg, W, label=""):
       that vanish on locally flat data);
     * the state after the step must agree within 1e-11.
     """
-    Wg, st, fg = gpu_step(cfg, W)
+    Wg, st, fg = gpu_step(cfg, W, t0=t0)
     Wstar = np.zeros_like(np.ascontiguousarray(W))
-    Wo, dt, fo, mo = oracle.step_flags(cfg, W, margins=True, wstar=Wstar)
+    Wo, dt, fo, mo = oracle.step_flags(cfg, W, margins=True, wstar=Wstar, t0=t0)
     assert st["last_dt"] == dt, (label, st["last_dt"], dt)
     assert set(fg) == set(fo)
     for key in fo:
@@ -74,7 +74,7 @@ def check_step(cfg, W, label=""):
             robust = diff & (mo[key] >= 1.0)
             assert int(robust.sum()) == 0, (label, key, "robust decision differs", np.argwhere(robust)[:4])
             assert int(diff.sum()) <= max(2, diff.size // 100), (label, key, int(diff.sum()))
-    _, _, f2 = gpu_step(cfg, Wstar, dt=dt)
+    _, _, f2 = gpu_step(cfg, Wstar, t0=t0 + 0.5 * dt, dt=dt)    # the second stage runs at t* = t0 + dt/2
     for key in fo:
         if key[0] == 1:
             k0 = (0, key[1], key[2])
@@ -257,3 +257,26 @@ def test_troubled_counters():
             assert st["troubled"][stage, sweep, 1] == sum(bin(int(v)).count("1") for v in ft.ravel())
             assert st["examined"][stage, sweep, 1] == 4 * ft.size
     s.hgks_destroy_solver()
+
+
+# ------------------------------------------------------------------ double Mach reflection (Sec. 3.5)
+
+def test_double_mach_steps_with_moving_shock_boundary():
+    """Inflow, the wall that starts at x = 1/6 and the top boundary that follows the shock,
+    at the first step and at later times (the boundary depends on the stage time)."""
+    cfg, W, _ = P.double_mach(64, 16)
+    check_step(cfg, W, "dmr t=0")
+    Wo, t, n, _ = oracle.run(cfg, W, 1.0, max_steps=20)
+    check_step(cfg, Wo, "dmr t=%g" % t, t0=t)
+
+
+def test_oblique_shock_run_matches_oracle():
+    cfg, W = P.oblique_shock(48, 24)
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(np.ascontiguousarray(W))
+    n = s.hgks_step(0.01, 1 << 20)
+    Wg, tg = s.hgks_get_state(), s.hgks_get_time()
+    s.hgks_destroy_solver()
+    Wo, to, no, _ = oracle.run(cfg, W, 0.01)
+    assert n == no and tg == to
+    assert rel_diff(Wg, Wo) <= 1e-10

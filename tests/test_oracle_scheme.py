@@ -269,3 +269,111 @@ def test_t_end_is_hit_exactly():
     cfg, W, _ = P.sod_1d(50)
     W2, t, steps, last = oracle.run(cfg, W, 0.0123)
     assert t == pytest.approx(0.0123, abs=1e-15) and last > 0
+
+
+# ---------------------------------------------------------------- double Mach reflection (Sec. 3.5)
+
+def _rh_residuals(post, pre, normal, speed, gamma=1.4):
+    """Rankine-Hugoniot residuals (relative) of a shock moving at `speed` along `normal`."""
+    def fluxes(state):
+        rho, u, v, p = state
+        un = u * normal[0] + v * normal[1]
+        ut = -u * normal[1] + v * normal[0]
+        E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+        w = un - speed
+        return np.array([rho * w, rho * un * w + p, rho * ut * w, E * w + p * un])
+    a, b = fluxes(post), fluxes(pre)
+    return np.abs(a - b) / np.maximum(np.abs(a), np.abs(b))
+
+
+def test_double_mach_states_satisfy_rankine_hugoniot():
+    """The printed post-/pre-shock states are the exact Mach 10 shock at 60 deg (the line
+    x = 1/6 + (y + 20 t)/sqrt(3) moves at 10 along its normal (sin 60, -cos 60))."""
+    cot = P.DMR_COT
+    sin = 1.0 / np.sqrt(1.0 + cot * cot)
+    normal = (sin, -cot * sin)
+    speed = P.DMR_SPEED * cot * sin
+    assert speed == pytest.approx(10.0, rel=1e-15)
+    res = _rh_residuals(P.DMR_POST, P.DMR_PRE, normal, speed)
+    assert np.all(res[[0, 1, 3]] <= 1e-13), res
+    assert abs(P.DMR_POST[0] * (P.DMR_POST[1] * -normal[1] + P.DMR_POST[2] * normal[0])) <= 1e-13   # no tangential jump
+    # Mach number of the normal shock in the pre-shock gas
+    assert speed / np.sqrt(1.4 * P.DMR_PRE[3] / P.DMR_PRE[0]) == pytest.approx(10.0, rel=1e-15)
+
+
+def _crossings(rho, x1):
+    """x where each row first drops through the mid density (linear interpolation between centres)."""
+    nx = rho.shape[1]
+    dx = x1 / nx
+    mid = 0.5 * (P.DMR_POST[0] + P.DMR_PRE[0])
+    out = []
+    for row in rho:
+        k = int(np.argmax(row < mid))
+        f = (row[k - 1] - mid) / (row[k - 1] - row[k])
+        out.append((k - 0.5 + f) * dx)
+    return np.array(out)
+
+
+def test_oblique_shock_travels_at_the_exact_speed():
+    """With inflow behind, the y-sides following the exact motion and a non-reflecting end,
+    the captured Mach 10 shock stays on the exact line in every row, including the rows next
+    to the moving boundaries (a boundary that lags the motion drags its rows behind)."""
+    n = 64
+    cfg, W = P.oblique_shock(n, n // 2)
+    Wo, t, steps, _ = oracle.run(cfg, W, 0.02)
+    assert steps > 10 and t == 0.02
+    yc = (np.arange(n // 2) + 0.5) * (0.5 / (n // 2))
+    exact = P.DMR_X0 + P.DMR_COT * (yc + P.DMR_SPEED * t)
+    got = _crossings(Wo[0], 1.0)
+    assert np.max(np.abs(got - exact)) <= 1.0 / n, np.abs(got - exact).max() * n
+    # planting a frozen boundary (the line not moving with time) moves the boundary rows
+    frozen = dict(cfg, shock_speed=0.0)
+    Wf, _, _, _ = oracle.run(frozen, W, 0.02)
+    bad = np.abs(_crossings(Wf[0], 1.0) - exact)
+    assert max(bad[0], bad[-1]) > 2.0 / n
+
+
+def test_double_mach_robust_and_quiet_ahead_of_the_shock():
+    """The full problem runs to a later time at CFL 0.8 with positive density and pressure,
+    and the gas at rest more than 8 cells ahead of the shock stays at rest to 1e-8 (only the
+    high-order stencils' far tails reach it)."""
+    nx, ny = 96, 24
+    cfg, W, _ = P.double_mach(nx, ny)
+    Wo, t, steps, _ = oracle.run(cfg, W, 0.05)
+    assert t == 0.05
+    rho = Wo[0]
+    p = 0.4 * (Wo[3] - 0.5 * (Wo[1] ** 2 + Wo[2] ** 2) / rho)
+    assert rho.min() > 0 and p.min() > 0
+    xc = (np.arange(nx) + 0.5) * (4.0 / nx)
+    yc = (np.arange(ny) + 0.5) * (1.0 / ny)
+    ahead = xc[None, :] > P.DMR_X0 + P.DMR_COT * (yc[:, None] + P.DMR_SPEED * t) + 8 * (4.0 / nx)
+    pre = P.conservative(*P.DMR_PRE)
+    scale = np.abs(pre).max()
+    for k in range(4):
+        assert np.max(np.abs(Wo[k][ahead] - pre[k])) <= 1e-8 * scale
+    assert ahead.sum() > nx * ny // 4
+
+
+def test_prescribed_boundary_ghosts():
+    """Inflow ghosts hold the prescribed state; the shock wall is the prescribed state up to
+    x = 1/6 and a slip wall beyond; the tracking boundary switches at the shock line."""
+    nx, ny = 24, 6
+    cfg, W, _ = P.double_mach(nx, ny)
+    NG = oracle.NG
+    t = 0.03
+    Wp = oracle.fill_ghosts(cfg, W, t)
+    post, pre = P.conservative(*P.DMR_POST), P.conservative(*P.DMR_PRE)
+    dx, dy = 4.0 / nx, 1.0 / ny
+    for l in range(1, NG + 1):
+        np.testing.assert_array_equal(Wp[:, NG:NG + ny, NG - l], np.repeat(post[:, None], ny, axis=1))
+        for i in range(-NG, nx + NG):
+            xc = (i + 0.5) * dx
+            g = Wp[:, NG - l, NG + i]
+            if xc < P.DMR_X0:
+                np.testing.assert_array_equal(g, post)
+            elif 0 <= i < nx:
+                m = W[:, l - 1, i].copy(); m[2] = -m[2]
+                np.testing.assert_array_equal(g, m)
+            yc = (ny - 1 + l + 0.5) * dy
+            behind = xc < P.DMR_X0 + P.DMR_COT * (yc + P.DMR_SPEED * t)
+            np.testing.assert_array_equal(Wp[:, NG + ny - 1 + l, NG + i], post if behind else pre)
