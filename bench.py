@@ -275,6 +275,37 @@ def bench_served(args, torch, hgks, P):
     print(json.dumps(line), flush=True)
 
 
+def bench_ns_tube(args, torch, hgks, P):
+    """2D Navier-Stokes viscous shock tube in [0,1] x [0,0.5] (Sec. 3.6 set-up) at Re = 1000,
+    Pr = 0.73 (energy-flux Prandtl fix), nx x nx/2 cells: K timed S2O4 steps on the device."""
+    nx = args.ns_nx
+    cfg, W, _ = P.viscous_shock_tube(nx, nx // 2, Re=1000.0, prandtl=0.73)
+    stream = torch.cuda.Stream()
+    s = hgks.Solver(cfg, stream=stream)
+    s.hgks_set_state(np.ascontiguousarray(W))
+    s.hgks_step(1.0, args.warmup, wait=True)
+    s.hgks_set_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s.hgks_step(1.0, args.steps, wait=False)
+    b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    tim = s.hgks_get_timing()
+    st = s.hgks_get_stats()
+    s.hgks_destroy_solver()
+    cells = nx * (nx // 2)
+    tot = sum(v[0] for v in tim.values())
+    line = {"metric": METRIC, "workload": "2D NS viscous shock tube, %dx%d, Re 1000, Pr 0.73, hybrid, S2O4" % (nx, nx // 2),
+            "unit": UNIT, "value": cells * 2 * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "status": int(st["status"]), "t": st["t"],
+            "troubled_fraction": float(st["troubled"].sum()) / max(1, int(st["examined"].sum())),
+            "kernel_time_share": {k: round(v[0] / max(1e-9, tot), 4) for k, v in tim.items() if v[1]},
+            "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+    print(json.dumps(line), flush=True)
+
+
 RECON_CLASSES = ("raw_normal_flags", "normal_recon", "normal_weno_ao", "raw_tangential_flags", "tangential_recon",
                  "tangential_weno_ao")
 
@@ -348,7 +379,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ref-side", type=int, default=256, help="grid side of the oracle's bounded sample")
-    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost"])
+    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube"])
+    ap.add_argument("--ns-nx", type=int, default=1000, help="ns_tube: cells along x (ny = nx/2)")
     ap.add_argument("--recon-cases", default="", help="comma-separated subset of the recon_cost cases")
     ap.add_argument("--solves", type=int, default=256)
     ap.add_argument("--requests", type=int, default=32)
@@ -387,6 +419,8 @@ def main():
         return bench_served(args, torch, hgks, P)
     if args.workload == "recon_cost":
         return bench_recon_cost(args, torch, hgks, P)
+    if args.workload == "ns_tube":
+        return bench_ns_tube(args, torch, hgks, P)
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)

@@ -63,7 +63,10 @@ typedef struct hgks_config {
     double x0, x1, y0, y1;    /* domain [x0,x1] x [y0,y1] */
     double gamma;             /* ratio of specific heats (Sec. 3: 1.4) */
     int viscous;              /* 0: Euler, tau = c1 dt + c2 |pl-pr|/(pl+pr) dt; 1: Navier-Stokes, tau = mu/p + c2 ... (Sec. 3) */
-    double mu, prandtl;       /* dynamic viscosity (1/Re); Prandtl number (only Pr = 1, the BGK value, is accepted) */
+    double mu, prandtl;       /* dynamic viscosity (1/Re); Prandtl number.  The paper's BGK flux has Pr = 1;
+                                 for viscous runs with Pr != 1 the energy flux gains (1/Pr - 1) q, q the
+                                 time-integrated heat flux of the interface distribution of Eq. (10) relative
+                                 to the equilibrium velocity (an extension; Pr = 1 leaves the flux untouched) */
     double c1, c2;            /* collision-time constants (Sec. 3) */
     double cfl;               /* dt = cfl min(h/(|U|+a), h^2/(4 nu)), h = min(dx, dy), nu = mu/rho */
     double fixed_dt;          /* > 0: use this dt instead of the CFL rule (Sec. 3.1 uses dt = 0.2 dx) */

@@ -26,6 +26,7 @@
  * Readings of points the paper leaves open are marked "Reading:".
  */
 #include <math.h>
+#include <stdio.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -34,7 +35,8 @@
 #endif
 
 #define NG 4        /* ghost layers: the widest indicator window (Step 4 spread of a 5-cell test) reaches 4 cells */
-#define MAXT 160    /* terms of a polynomial in (u, v, xi^2) */
+#define MAXT 256    /* terms of a polynomial in (u, v, xi^2); the largest product formed (heat
+                       weight of 18 terms x slope polynomial of 12 terms) has 216 */
 #define NMOM 10     /* highest velocity power needed is u^7 (flux of the slope term) */
 
 enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4,
@@ -86,6 +88,7 @@ typedef struct {
 static void p_set(poly* p) { p->n = 0; }
 static void p_term(poly* p, double c, int a, int b, int x)
 {
+    if (p->n >= MAXT) { fprintf(stderr, "hgks oracle: polynomial term overflow\n"); abort(); }
     p->c[p->n] = c; p->pu[p->n] = (unsigned char)a; p->pv[p->n] = (unsigned char)b;
     p->px[p->n] = (unsigned char)x; p->n++;
 }
@@ -350,6 +353,46 @@ static int gks_point_flux(const or_config* cfg, const double* Wl, const double* 
     p_mul(&t, &uu, &t); integ_psi(dim, &t, &mr, -1, R5);
     slope_poly(dim, Ar, &pa); p_mul(&pa, &uu, &t); integ_psi(dim, &t, &mr, -1, R6);
 
+    /* Prandtl-number fix (not in the paper, whose BGK flux has Pr = 1): for a viscous
+       run with Pr != 1 the energy flux gains (1/Pr - 1) q, where q is the time-integrated
+       heat flux of the interface distribution of Eq. (10),
+         q(d) = int_0^d int (u - Uc) (|u - Uc|^2 + xi^2)/2 f dXi dt,
+       with (Uc, Vc) the velocity of the equilibrium state W^c: each of the six terms of
+       Eq. (10) integrated against h = (u-Uc)((u-Uc)^2 + (v-Vc)^2 + xi^2)/2 instead of u psi. */
+    double hM[3] = {0, 0, 0}, hL[3] = {0, 0, 0}, hR[3] = {0, 0, 0};
+    int prfix = cfg->viscous && cfg->prandtl != 1.0;
+    if (prfix) {
+        poly cu, cv, xi2, s2, h, w;
+        p_set(&cu); p_term(&cu, 1.0, 1, 0, 0); p_term(&cu, -Uc, 0, 0, 0);
+        p_set(&cv); p_term(&cv, 1.0, 0, 1, 0); p_term(&cv, -Vc, 0, 0, 0);
+        p_set(&xi2); p_term(&xi2, 1.0, 0, 0, 1);
+        p_mul(&cu, &cu, &s2);
+        if (dim == 2) { p_mul(&cv, &cv, &w); p_add(&s2, &w, &s2); }
+        p_add(&s2, &xi2, &s2);
+        p_mul(&cu, &s2, &h);
+        for (int i = 0; i < h.n; i++) h.c[i] *= 0.5;
+        /* g0, (ab1 u + ab2 v) g0, Ab g0 */
+        hM[0] = integ(&h, &mc, 0);
+        slope_poly(dim, ab1, &pa); p_mul(&pa, &uu, &t);
+        if (dim == 2) { slope_poly(dim, ab2, &pa); p_mul(&pa, &vv, &t2); p_add(&t, &t2, &t); }
+        p_mul(&t, &h, &w); hM[1] = integ(&w, &mc, 0);
+        slope_poly(dim, Ab, &pa); p_mul(&pa, &h, &w); hM[2] = integ(&w, &mc, 0);
+        /* each side over its half line: g^k, (a1^k u + a2^k v) g^k, A^k g^k */
+        for (int side = 0; side < 2; side++) {
+            const mom* ms = side == 0 ? &ml : &mr;
+            int half = side == 0 ? +1 : -1;
+            const double* a1 = side == 0 ? a1l : a1r;
+            const double* a2 = side == 0 ? a2l : a2r;
+            const double* A = side == 0 ? Al : Ar;
+            double* out = side == 0 ? hL : hR;
+            out[0] = integ(&h, ms, half);
+            slope_poly(dim, a1, &pa); p_mul(&pa, &uu, &t);
+            if (dim == 2) { slope_poly(dim, a2, &pa); p_mul(&pa, &vv, &t2); p_add(&t, &t2, &t); }
+            p_mul(&t, &h, &w); out[1] = integ(&w, ms, half);
+            slope_poly(dim, A, &pa); p_mul(&pa, &h, &w); out[2] = integ(&w, ms, half);
+        }
+    }
+
     /* Reading: in Eq. (10) particles with u > 0 arrive from the left state (the
        printed H(u) / (1-H(u)) labels are swapped with respect to Eq. (7)). */
     for (int pass = 0; pass < 2; pass++) {
@@ -372,6 +415,11 @@ static int gks_point_flux(const or_config* cfg, const double* Wl, const double* 
         for (int k = 0; k < nv; k++)
             out[k] = C1 * M1[k] + C2 * M2[k] + C3 * M3[k]
                    + C4 * (L4[k] + R4[k]) + C5 * (L5[k] + R5[k]) + C6 * (L6[k] + R6[k]);
+        if (prfix) {
+            double q = C1 * hM[0] + C2 * hM[1] + C3 * hM[2]
+                     + C4 * (hL[0] + hR[0]) + C5 * (hL[1] + hR[1]) + C6 * (hL[2] + hR[2]);
+            out[nv - 1] += (1.0 / cfg->prandtl - 1.0) * q;
+        }
     }
     return OR_OK;
 }

@@ -55,8 +55,8 @@ int validate(const hgks_config* c, char* err)
     if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) { set_err(err, "gamma must be > 1"); return HGKS_EINVAL; }
     if (!(c->fixed_dt > 0.0) && !(c->cfl > 0.0)) { set_err(err, "need cfl > 0 or fixed_dt > 0"); return HGKS_EINVAL; }
     if (c->viscous && !(c->mu > 0.0)) { set_err(err, "viscous run needs mu > 0"); return HGKS_EINVAL; }
-    if (c->viscous && c->prandtl != 1.0) {
-        set_err(err, "only Pr = 1 (the BGK value of the paper's flux) is supported (got %g)", c->prandtl);
+    if (c->viscous && !(c->prandtl > 0.0 && std::isfinite(c->prandtl))) {
+        set_err(err, "the Prandtl number must be > 0 (got %g)", c->prandtl);
         return HGKS_EINVAL;
     }
     if (c->c1 < 0.0 || c->c2 < 0.0) { set_err(err, "c1, c2 must be >= 0"); return HGKS_EINVAL; }
@@ -110,6 +110,7 @@ void fill_params(const hgks_config* c, Params& P)
     P.gamma = c->gamma; P.K = dof_K(c->dim, c->gamma); P.mu = c->mu; P.c1 = c->c1; P.c2 = c->c2;
     P.cfl = c->cfl; P.fixed_dt = c->fixed_dt;
     P.viscous = c->viscous; P.tau_zero = c->tau_zero; P.recon_mode = c->recon_mode;
+    P.prfix = (c->viscous && c->prandtl != 1.0) ? 1.0 / c->prandtl - 1.0 : 0.0;
     for (int k = 0; k < 4; k++) P.bc[k] = c->bc[k];
     P.x0 = c->x0; P.y0 = c->dim == 2 ? c->y0 : 0.0;
     for (int k = 0; k < 4; k++)

@@ -62,6 +62,7 @@ struct Sweep {
 struct Params {
     GridGeom g;
     double gamma, K, mu, c1, c2, cfl, fixed_dt;
+    double prfix;                  // 1/Pr - 1 (viscous runs with Pr != 1), else 0
     int viscous, tau_zero, recon_mode;
     int bc[4];
     double g_ao[4], g3inv, gr[3], eps;

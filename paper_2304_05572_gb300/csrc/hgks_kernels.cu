@@ -549,7 +549,7 @@ __global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const
 
 
 // ---------------------------------------------------------------- flux and update
-template <int DIM, int STAGE>
+template <int DIM, int STAGE, bool PRFIX>
 __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ctrl, long long id)
 {
     if (ctrl->done) return;
@@ -581,8 +581,9 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
     fc.gamma = P.gamma; fc.gm1 = P.gamma - 1.0; fc.K = P.K;
     fc.Kq = P.K + (double)DIM; fc.cslope = 4.0 / fc.Kq;
     fc.mu = P.mu; fc.c1 = P.c1; fc.c2 = P.c2; fc.viscous = P.viscous; fc.tau_zero = P.tau_zero;
+    fc.prfix = P.prfix;
     double o0[NV], o1[NV];
-    bool ok = gks_flux<DIM, STAGE>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1);
+    bool ok = gks_flux<DIM, STAGE, PRFIX>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1);
     if (!ok) { ctrl->status = HGKS_ENONPHYSICAL; return; }
 #pragma unroll
     for (int k = 0; k < NV; k++) {
@@ -592,10 +593,18 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
     }
 }
 
-template <int DIM, int STAGE>
+template <int DIM, int STAGE, bool PRFIX>
 __global__ void __launch_bounds__(128) k_flux(Params P, Sweep S, Ctrl* ctrl)
 {
-    b_flux<DIM, STAGE>(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_flux<DIM, STAGE, PRFIX>(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// the Prandtl-fix flux as a separate (not inlined) function for the batched kernel, whose
+// blocks may belong to solvers with and without the fix
+template <int DIM, int STAGE>
+__device__ __noinline__ void b_flux_prfix(const Params& P, const Sweep& S, Ctrl* ctrl, long long id)
+{
+    b_flux<DIM, STAGE, true>(P, S, ctrl, id);
 }
 
 
@@ -772,7 +781,8 @@ template <int DIM, int STAGE>
 __global__ void __launch_bounds__(256) kb_flux(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
 {
     HGKS_BATCH_BLOCK();
-    b_flux<DIM, STAGE>(d.P, d.sw[dir], d.ctrl, id);
+    if (d.P.prfix != 0.0) b_flux_prfix<DIM, STAGE>(d.P, d.sw[dir], d.ctrl, id);
+    else b_flux<DIM, STAGE, false>(d.P, d.sw[dir], d.ctrl, id);
 }
 
 template <int DIM, int STAGE>
@@ -862,8 +872,14 @@ static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
     }
     timed(s, KC_FLUX, 1, [&] {
         long long n = (long long)S.nt * S.nm * (DIM == 2 ? 2 : 1);
-        if (stage == 0) k_flux<DIM, 0><<<blocks_for(n, 128), 128, 0, st>>>(P, S, ctrl);
-        else k_flux<DIM, 1><<<blocks_for(n, 128), 128, 0, st>>>(P, S, ctrl);
+        const unsigned int nb = blocks_for(n, 128);
+        if (P.prfix != 0.0) {
+            if (stage == 0) k_flux<DIM, 0, true><<<nb, 128, 0, st>>>(P, S, ctrl);
+            else k_flux<DIM, 1, true><<<nb, 128, 0, st>>>(P, S, ctrl);
+        } else {
+            if (stage == 0) k_flux<DIM, 0, false><<<nb, 128, 0, st>>>(P, S, ctrl);
+            else k_flux<DIM, 1, false><<<nb, 128, 0, st>>>(P, S, ctrl);
+        }
     });
 }
 

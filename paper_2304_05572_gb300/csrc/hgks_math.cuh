@@ -342,8 +342,18 @@ struct MState {
 
 struct FluxConst {
     double gamma, gm1, K, Kq, cslope, mu, c1, c2;   // Kq = K + D (D = 2 in 2D, 1 in 1D), cslope = 4/Kq
+    double prfix;                                    // 1/Pr - 1 for viscous runs with Pr != 1, else 0
     int viscous, tau_zero;
 };
+
+template <int NV>
+HGKS_HD __forceinline__ double dotv(const double* a, const double* b)
+{
+    double s = a[0] * b[0];
+#pragma unroll
+    for (int k = 1; k < NV; k++) s = fma(a[k], b[k], s);
+    return s;
+}
 
 template <int DIM>
 HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MState<DIM>& s)
@@ -598,7 +608,7 @@ HGKS_HD __forceinline__ void psi_mom(const Mom<DIM>& m, double* out0, double* ou
 //   STAGE 0: o0 = Fh (for W*, Eq. (19)),  o1 = (8 Fh - Fd)/3 = dt F^n + dt^2/6 dF^n (Eqs. (17)-(18), (20))
 //   STAGE 1: o0 = (4/3)(Fd - 2 Fh) = dt^2/3 dF* (Eqs. (18), (20))
 // Returns false if a side or the equilibrium state is non-physical.
-template <int DIM, int STAGE>
+template <int DIM, int STAGE, bool PRFIX = false>
 HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, const double* Wlx, const double* Wly,
                                          const double* Wr, const double* Wrx, const double* Wry, double dt,
                                          double* o0, double* o1)
@@ -709,6 +719,23 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
             acc0[k] = fma(A0[1], M2[k], acc0[k]);
             acc1[k] = fma(A1[1], M2[k], acc1[k]);
         }
+        // Prandtl-number fix (an extension: the paper's BGK flux has Pr = 1).  The energy flux
+        // gains (1/Pr - 1) q, q the time-integrated heat flux of the distribution of Eq. (10)
+        // relative to the equilibrium velocity (Uc, Vc).  With l = (|Uc|^2/2, -Uc, -Vc, 1),
+        // int (u - Uc)(|u - Uc|^2 + xi^2)/2 phi = l.(int u psi phi) - Uc l.(int psi phi) for
+        // every term phi of Eq. (10); the g0 term carries no heat flux, the density moments of
+        // the (abar u) g0 and Abar g0 terms are -Wc_t and Wc_t (compatibility, Eq. (9)).
+        // (a compile-time variant, so that the Pr = 1 flux keeps its register allocation)
+        double lv[NV], Qh[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if constexpr (PRFIX) {
+            lv[0] = 0.5 * fma(sc.U, sc.U, sc.V * sc.V);
+            lv[1] = -sc.U;
+            if constexpr (DIM == 2) lv[2] = -sc.V;
+            lv[NV - 1] = 1.0;
+            const double lWt = dotv<NV>(lv, Wct);
+            Qh[1] = fma(sc.U, lWt, dotv<NV>(lv, M2));
+            Qh[2] = fma(-sc.U, lWt, dotv<NV>(lv, M3));
+        }
         // non-equilibrium initial parts: left state over u > 0, right state over u < 0, with the
         // time slope A from the compatibility condition <a1 u + a2 v + A> = 0 (Eq. (9))
 #pragma unroll
@@ -735,6 +762,28 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
                 acc0[k] = fma(st.rho, fma(A0[3], L4[k], fma(A0[4], L5[k], A0[5] * L6[k])), acc0[k]);
                 acc1[k] = fma(st.rho, fma(A1[3], L4[k], fma(A1[4], L5[k], A1[5] * L6[k])), acc1[k]);
             }
+            if constexpr (PRFIX) {
+                // density moments of the side's three terms over its half line
+                double D5[NV], D6[NV];
+                Gm<DIM, 1, 0>(a1, mh, D5);
+                if constexpr (DIM == 2) {
+                    Gm<DIM, 0, 1>(a2, mh, t1);
+#pragma unroll
+                    for (int k = 0; k < NV; k++) D5[k] += t1[k];
+                }
+                Gm<DIM, 0, 0>(As, mh, D6);
+                const double* D4 = side == 0 ? pl0 : pr0;
+                Qh[3] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D4), dotv<NV>(lv, L4)), Qh[3]);
+                Qh[4] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D5), dotv<NV>(lv, L5)), Qh[4]);
+                Qh[5] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D6), dotv<NV>(lv, L6)), Qh[5]);
+            }
+        }
+        if constexpr (PRFIX) {
+            double q0 = 0.0, q1 = 0.0;
+#pragma unroll
+            for (int j = 1; j < 6; j++) { q0 = fma(A0[j], Qh[j], q0); q1 = fma(A1[j], Qh[j], q1); }
+            acc0[NV - 1] = fma(fc.prfix, q0, acc0[NV - 1]);
+            acc1[NV - 1] = fma(fc.prfix, q1, acc1[NV - 1]);
         }
     }
 #pragma unroll

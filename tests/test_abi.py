@@ -50,7 +50,10 @@ def test_config_default_layout(L):
     (dict(gamma=1.0), "gamma"),
     (dict(cfl=0.0, fixed_dt=0.0), "cfl"),
     (dict(viscous=1, mu=0.0), "mu"),
-    (dict(viscous=1, mu=1e-3, prandtl=0.73), "Pr"),
+    (dict(viscous=1, mu=1e-3, prandtl=0.0), "Prandtl"),
+    (dict(bc=["periodic", "periodic", "extrap", "shock_wall"]), "SHOCK_WALL"),
+    (dict(bc=["shock_track", "extrap", "extrap", "extrap"]), "SHOCK_TRACK"),
+    (dict(bc=["inflow", "extrap", "extrap", "extrap"]), "prescribed"),
     (dict(bc=["periodic", "extrap", "extrap", "extrap"]), "periodic"),
     (dict(recon_mode=7), "recon"),
     (dict(gamma_hi=1.0), "gamma_hi"),

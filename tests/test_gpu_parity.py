@@ -161,6 +161,24 @@ def test_viscous_shock_tube_steps():
         W, _, _, _ = check_step(cfg, W, "vst step %d" % n)
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_prandtl_fix_steps(dim):
+    """Viscous runs with Pr = 0.73 (the energy-flux Prandtl fix) against the oracle, which
+    integrates the heat-flux weight literally while the GPU forms it from flux and density
+    moments."""
+    if dim == 2:
+        cfg, W, _ = P.viscous_shock_tube(40, 20, Re=1000.0, prandtl=0.73)
+    else:
+        cfg, W, _ = P.sod_1d(64)
+        cfg = dict(cfg, viscous=1, mu=2e-3, prandtl=0.73)
+    W0 = W
+    for n in range(2):
+        W, _, _, _ = check_step(cfg, W, "Pr 0.73 step %d" % n)
+    # the fix changes the result (by far more than the tolerance) and only the energy flux
+    Wo1, _, _, _ = oracle.run(dict(cfg, prandtl=1.0), W0, 1.0, max_steps=2)
+    assert rel_diff(W, Wo1) > 1e-9
+
+
 def test_boundary_mix_and_tau_zero():
     cfg, W, _ = P.random_smooth_2d(20, 17)
     cfg["bc"] = ["periodic", "periodic", "reflect", "noslip"]

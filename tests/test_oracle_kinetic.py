@@ -132,16 +132,19 @@ def test_tau_zero_flux_is_lax_wendroff(dim):
 
 
 @pytest.mark.parametrize("dim", [1, 2])
-def test_viscous_flux_is_navier_stokes(dim):
+@pytest.mark.parametrize("prandtl", [1.0, 0.73, 2.0])
+def test_viscous_flux_is_navier_stokes(dim, prandtl):
     """With equal sides and tau = mu/p, F^n of Eq. (17) is the Chapman-Enskog
     Navier-Stokes flux of the BGK model (Pr = 1): stress mu(grad U + grad U^T - 2/(K+D) div U I),
-    heat flux -mu c_p grad T with c_p = (K + D + 2)/2."""
+    heat flux -mu c_p grad T with c_p = (K + D + 2)/2.  With the Prandtl-number fix of the
+    energy flux (an extension: the paper's flux has Pr = 1) the heat flux is -mu c_p/Pr grad T
+    and nothing else changes."""
     mu = 2e-3
     r, u, v, p = 1.3, 0.4, (-0.3 if dim == 2 else 0.0), 0.9
     W = _prim_to_cons(r, u, v, p, dim)
     Wx = np.array([0.1, -0.05, 0.07, 0.2]) if dim == 2 else np.array([0.1, -0.05, 0.2])
     Wy = np.array([-0.03, 0.02, 0.05, -0.1]) if dim == 2 else None
-    cfg = P.base_config(dim, 8, 8, 0, 1, viscous=1, mu=mu, c2=0.0)
+    cfg = P.base_config(dim, 8, 8, 0, 1, viscous=1, mu=mu, c2=0.0, prandtl=prandtl)
     d = 1e-3
     Fd, Fh = oracle.point_flux(cfg, W, Wx, W, Wx, d, Wly=Wy, Wry=Wy)
     Fn = (4 * Fh - Fd) / d
@@ -163,7 +166,7 @@ def test_viscous_flux_is_navier_stokes(dim):
     div = gx[0] + gy[1]
     sxx = mu * (2 * gx[0] - 2.0 / (K + dim) * div)
     sxy = mu * (gy[0] + gx[1])
-    q = -mu * (K + dim + 2) / 2 * gx[2]
+    q = -mu / prandtl * (K + dim + 2) / 2 * gx[2]
     FE = _euler_fluxes(W, dim)[0]
     if dim == 1:
         Fv = np.array([0.0, sxx, u * sxx - q])
