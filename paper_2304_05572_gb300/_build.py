@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libhgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hgks_kernels.cu", "hgks_api.cu"]
-HEADERS = ["hgks_math.cuh", "hgks_internal.h"]
+HEADERS = ["hgks_math.cuh", "hgks_internal.h", "erfcx_table.inc"]
 
 
 def _nvcc():

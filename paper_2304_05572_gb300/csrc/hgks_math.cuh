@@ -574,15 +574,50 @@ HGKS_HD __forceinline__ void full_moments(const MState<DIM>& s, const FluxConst&
     fill_vx<DIM>(s, fc, m);
 }
 
+#include "erfcx_table.inc"
+
+// erfcx(y) = exp(y^2) erfc(y) on [0, 8): per interval [k/4, (k+1)/4) a degree-11 polynomial in
+// y - (k + 1/2)/4 (Chebyshev interpolant, relative error 2.1e-16; gen_erfcx_table.py).
+// Read by device code only.
+__device__ const double c_erfcx[HGKS_ERFCX_INTERVALS * (HGKS_ERFCX_DEGREE + 1)] = HGKS_ERFCX_TABLE;
+
+// erfc(y) for y >= 0, given ey = exp(-y^2): ey erfcx(y) from the table below y = 8 (17 FP64
+// operations instead of a full erfc, which recomputes the exponential), the library erfc above.
+HGKS_HD __forceinline__ double erfc_nonneg(double y, double ey)
+{
+#ifdef __CUDA_ARCH__
+    if (y < 8.0) {
+        // k = round(4y - 1/2) in 0..31 (the interval whose centre is nearest): adding 1.5 2^52
+        // leaves the rounded integer in the low mantissa bits
+        constexpr double kRound = 6755399441055744.0;
+        const double z = fma(y, 4.0, -0.5) + kRound;
+        const int k = __double2loint(z);
+        const double t = y - fma(z - kRound, 0.25, 0.125);
+        const double* a = c_erfcx + k * (HGKS_ERFCX_DEGREE + 1);
+        double p = __ldg(a + HGKS_ERFCX_DEGREE);
+#pragma unroll
+        for (int j = HGKS_ERFCX_DEGREE - 1; j >= 0; j--) p = fma(p, t, __ldg(a + j));
+        return ey * p;
+    }
+#endif
+    (void)ey;
+    return erfc(y);
+}
+
 // Half-line moments of the left state over u > 0 (sign = +1) or of the right state over
 // u < 0 (sign = -1): <1> = erfc(-+sqrt(lam) U)/2, <u> = U <1> +- exp(-lam U^2)/(2 sqrt(pi lam)).
+// With x = sqrt(lam) U, erfc(-+x) is formed from E = erfc(|x|): the half line that the mean
+// velocity points into holds 1 - E/2 of the mass, the other E/2.
 template <int DIM>
 HGKS_HD __forceinline__ void half_moments(const MState<DIM>& s, int sign, const FluxConst& fc, Mom<DIM>& m)
 {
     const double sl = sqrt(s.lam);
     const double x = sl * s.U;
-    const double e = exp(-x * x) * (0.56418958354775628695 * s.h * sl);   // 1/sqrt(pi) h sqrt(lam)
-    m.u[0] = 0.5 * erfc(sign > 0 ? -x : x);
+    const double ex2 = exp(-x * x);
+    const double e = ex2 * (0.56418958354775628695 * s.h * sl);   // 1/sqrt(pi) h sqrt(lam)
+    const double E = erfc_nonneg(fabs(x), ex2);
+    const bool into = sign > 0 ? x >= 0.0 : x < 0.0;
+    m.u[0] = into ? fma(-0.5, E, 1.0) : 0.5 * E;
     m.u[1] = fma(s.U, m.u[0], sign > 0 ? e : -e);
     recur_u<DIM>(s, m);
     fill_vx<DIM>(s, fc, m);
