@@ -46,6 +46,9 @@ FLUX_FLOP_PER_GP_2D = (1710.6 + 1641.4) / 2
 # and 107.5 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
 # them: Gauss-point states in, per-Gauss-point fluxes out).
 FLUX_DRAM_BYTES_PER_GP = (113.1e6 + 114.2e6 + 106.7e6 + 107.5e6) / 4 / (2 * 512 * 513)
+# FP64 flop of one whole S2O4 step per cell-stage (all kernels, ncu DADD + DMUL + 2 x DFMA
+# over the 40 launches of one 512^2 four-quadrant step, troubled fraction 1.1 %).
+STEP_FLOP_PER_CELL_STAGE = 8855.0
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 
@@ -261,7 +264,7 @@ def bench_served(args, torch, hgks, P):
         same = same and np.array_equal(out, res[r["id"]]["W"])
     plain_wall = time.perf_counter() - t0
     plain_lat = np.array([done_at[r["id"]] for r in trace])
-    line = {"metric": METRIC, "workload": "served: %d requests, Poisson rate %.0f/s (PCG64 seed %d), mix of 1D shock "
+    line = {"metric": METRIC, "workload": "served: %d requests, Poisson rate %.1f/s (PCG64 seed %d), mix of 1D shock "
             "tubes <= %d cells, 2D Riemann/vortex <= %d^2, 2D NS shock tubes <= %dx%d, t_end ~ U[0.05, 0.3], "
             "budget %.0f GB" % (len(trace), args.rate, P.SERVE_SEED, args.max_1d, args.max_2d, args.max_ns,
                                 args.max_ns // 2, args.budget_gb),
@@ -505,6 +508,10 @@ def main():
             roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                         "frac": None, "traffic": None, "kernel": "gks_flux", "avg_launch_ms": avg_ms}
     shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in timing.values())), 4) for k, v in timing.items() if v[1]}
+    if roofline is not None:
+        step_tflops = STEP_FLOP_PER_CELL_STAGE * value / world * 1e6 / 1e12
+        roofline["whole_step"] = {"flop_per_cell_stage": STEP_FLOP_PER_CELL_STAGE, "achieved": step_tflops,
+                                  "frac": step_tflops / (FP64_PEAK_GFLOPS / 1e3), "unit": "TFLOP/s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_timed,
@@ -525,8 +532,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             v, secs, cores = cpu_oracle_rate(N_SIDE, 1)
+            v1, secs1, _ = cpu_oracle_rate(256, 1, threads=1)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": "1 S2O4 step of the same 1024^2 problem (%.1f s)" % secs}
+                                    "sample": "1 S2O4 step of the same 1024^2 problem (%.1f s)" % secs,
+                                    "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                      "sample": "1 S2O4 step of the problem at 256^2 (%.1f s)" % secs1}}
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
     if rank == 0:
