@@ -206,6 +206,12 @@ int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, int flags);
  * returns HGKS_OK unless a CUDA call failed (HGKS_ECUDA). */
 int hgks_batch_sync(hgks_batch* b, int* n_active, int* n_failed);
 
+/* Per-solver time, latched status (0 or HGKS_ENONPHYSICAL) and step count as of the
+ * last hgks_batch_sync, in batch order; no wait, no device access.  Each output
+ * array (length n) may be NULL.  Lets a scheduler retire solvers without a
+ * round trip per solver. */
+int hgks_batch_status(const hgks_batch* b, double* t, int* status, long long* steps);
+
 /* Block size chosen for each kernel class (up to cap entries) and the number of
  * batched steps enqueued so far; returns the number of kernel classes. */
 int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long* steps_enqueued);

@@ -651,6 +651,18 @@ extern "C" int hgks_batch_sync(hgks_batch* b, int* n_active, int* n_failed)
     return HGKS_OK;
 }
 
+extern "C" int hgks_batch_status(const hgks_batch* b, double* t, int* status, long long* steps)
+{
+    if (!b) return HGKS_EINVAL;
+    for (int i = 0; i < b->n; i++) {
+        const Ctrl& c = *b->solvers[i]->ctrl_host;
+        if (t) t[i] = c.t;
+        if (status) status[i] = c.status;
+        if (steps) steps[i] = c.steps;
+    }
+    return HGKS_OK;
+}
+
 extern "C" int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long* steps_enqueued)
 {
     if (!b) return HGKS_EINVAL;

@@ -33,7 +33,8 @@ EXPORTED = [
     "hgks_config_default", "hgks_create_solver", "hgks_destroy_solver", "hgks_set_state", "hgks_step",
     "hgks_get_state", "hgks_get_time", "hgks_get_stats", "hgks_set_flag_capture", "hgks_flags_size",
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
-    "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_info", "hgks_batch_last_error",
+    "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status", "hgks_batch_info",
+    "hgks_batch_last_error",
     "hgks_batch_destroy", "hgks_step_noalloc",
 ]
 HGKS_BATCH_GRAPH = 1
@@ -106,6 +107,7 @@ def lib():
         L.hgks_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.hgks_batch_step.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int]
         L.hgks_batch_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.hgks_batch_status.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
         L.hgks_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
         L.hgks_batch_last_error.argtypes = [vp]
         L.hgks_batch_last_error.restype = ctypes.c_char_p
@@ -298,6 +300,15 @@ class Batch:
         n, f = ctypes.c_int(0), ctypes.c_int(0)
         self._check(lib().hgks_batch_sync(self._h, ctypes.byref(n), ctypes.byref(f)))
         return n.value, f.value
+
+    def hgks_batch_status(self):
+        """(t, status, steps) arrays of the solvers as of the last hgks_batch_sync."""
+        n = len(self.solvers)
+        t = (ctypes.c_double * n)()
+        st = (ctypes.c_int * n)()
+        steps = (ctypes.c_longlong * n)()
+        self._check(lib().hgks_batch_status(self._h, t, st, steps))
+        return list(t), list(st), list(steps)
 
     def hgks_batch_info(self):
         tpb = (ctypes.c_int * 64)()

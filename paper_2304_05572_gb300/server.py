@@ -5,7 +5,8 @@ The server admits a request as soon as its arrival time has passed and the
 device memory its solver needs (hgks_footprint_bytes) fits in the budget;
 admitted solves keep their state resident on the device and advance together:
 every iteration issues one batched group of S2O4 steps (hgks_batch_step, CUDA
-graph replay) per dimension for all resident solves, so newly admitted solves
+graph replay) per dimension for all resident solves, the 1D and 2D groups on
+their own streams so that they overlap on the device, so newly admitted solves
 overlap on the device with the ones already running.  A solve retires at its
 end time (or when its state turned non-physical: the scheme has no positivity
 limiter, and the status is reported with the result); its state is copied
@@ -29,28 +30,31 @@ class Server:
     def __init__(self, budget_bytes: float, stream=None, steps_per_iter: int = 4, autotune: bool = False):
         import torch
         self.budget = float(budget_bytes)
-        self.stream = stream if stream is not None else torch.cuda.Stream()
+        # one stream per dimension: the 1D batch (small, latency-bound launches) overlaps on the
+        # device with the 2D batch; `stream`, if given, serves the 2D solves
+        self.streams = {1: torch.cuda.Stream(), 2: stream if stream is not None else torch.cuda.Stream()}
         self.steps_per_iter = int(steps_per_iter)
         self.autotune = autotune
         self.used = 0.0
         self.active = {}          # id -> dict(req, solver, bytes, t_admit)
-        self.results = {}         # id -> dict(W, latency, admitted, completed, steps, t)
+        self.results = {}         # id -> dict(W, latency, admitted, completed, steps, t, status, cells)
         self._batches = {}        # dim -> (tuple of ids, Batch)
         self.iterations = 0
         self.peak_resident = 0
 
     def _admit(self, req, now):
-        s = hgks.Solver(req["cfg"], stream=self.stream)
+        dim = int(req["cfg"]["dim"])
+        s = hgks.Solver(req["cfg"], stream=self.streams[dim])
         s.hgks_set_state(np.ascontiguousarray(req["W"]))
         self.active[req["id"]] = dict(req=req, solver=s, bytes=req["bytes"], t_admit=now)
         self.used += req["bytes"]
         self.peak_resident = max(self.peak_resident, len(self.active))
 
-    def _retire(self, rid, now, st):
+    def _retire(self, rid, now, t, status, steps):
         a = self.active.pop(rid)
         s = a["solver"]
         self.results[rid] = dict(W=s.hgks_get_state(), latency=now - a["req"]["arrival"], admitted=a["t_admit"],
-                                 completed=now, steps=int(st["steps"]), t=st["t"], status=st["status"],
+                                 completed=now, steps=int(steps), t=t, status=int(status),
                                  cells=int(np.prod(a["req"]["W"].shape[1:])))
         s.hgks_destroy_solver()
         self.used -= a["bytes"]
@@ -62,7 +66,7 @@ class Server:
             return cur[1]
         if cur is not None:
             cur[1].hgks_batch_destroy()
-        b = hgks.Batch([self.active[i]["solver"] for i in key], stream=self.stream)
+        b = hgks.Batch([self.active[i]["solver"] for i in key], stream=self.streams[dim])
         self._batches[dim] = (key, b)
         return b
 
@@ -88,24 +92,28 @@ class Server:
                 continue
             by_dim = {}
             for rid, a in self.active.items():
-                by_dim.setdefault(a["req"]["cfg"]["dim"], []).append(rid)
-            for dim, ids in by_dim.items():
+                by_dim.setdefault(int(a["req"]["cfg"]["dim"]), []).append(rid)
+            stepped = []
+            for dim, ids in by_dim.items():             # enqueue every dimension first (they overlap)
                 b = self._batch_for(dim, ids)
                 key = self._batches[dim][0]
                 b.hgks_batch_step([self.active[i]["req"]["t_end"] for i in key], nsteps=self.steps_per_iter,
                                   graph=True, autotune=self.autotune)
+                stepped.append(dim)
             self.iterations += 1
-            for dim, (key, b) in list(self._batches.items()):
-                if dim not in by_dim:
-                    continue
+            finished = []
+            for dim in stepped:
+                key, b = self._batches[dim]
                 b.hgks_batch_sync()
+                ts, sts, nsteps = b.hgks_batch_status()
+                for rid, t, st, n in zip(key, ts, sts, nsteps):
+                    te = self.active[rid]["req"]["t_end"]
+                    # a solve retires at its end time, or with its error once its state turned non-physical
+                    if st != 0 or te - t <= 1e-12 * max(1.0, abs(te)):
+                        finished.append((rid, t, st, n))
             now = time.perf_counter() - t0
-            for rid in list(self.active):
-                st = self.active[rid]["solver"].hgks_get_stats()
-                te = self.active[rid]["req"]["t_end"]
-                # a solve retires at its end time, or with its error once its state turned non-physical
-                if st["status"] != 0 or te - st["t"] <= 1e-12 * max(1.0, abs(te)):
-                    self._retire(rid, now, st)
+            for rid, t, st, n in finished:
+                self._retire(rid, now, t, st, n)
         for dim, (key, b) in list(self._batches.items()):
             b.hgks_batch_destroy()
         self._batches.clear()

@@ -115,6 +115,10 @@ def test_failed_solver_stops_alone_and_others_continue():
     b.hgks_batch_step([1e9] * 3, nsteps=12, graph=True)
     active, failed = b.hgks_batch_sync()
     assert failed == 1 and active == 2
+    ts, sts, ns = b.hgks_batch_status()
+    for s, t, st, n in zip(solvers, ts, sts, ns):
+        ref = s.hgks_get_stats()
+        assert (t, st, n) == (ref["t"], ref["status"], ref["steps"])
     for (cfg, W), s in zip(cases, solvers):
         ref, t_ref, n_ref = _alone(cfg, W, 1e9, 12)
         st = s.hgks_get_stats()
