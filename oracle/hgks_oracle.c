@@ -653,13 +653,15 @@ static void eigvec(int dim, double gam, const double* Q, double nx, double ny, d
 
 /* Reading (the paper states no safeguard): a reconstructed state with rho <= 0
  * or p <= 0 is replaced by the first-order one (the average it was reconstructed
- * in, with zero slope).  The test, in this fixed order:
- *   ke = 0.5 (m_x^2 + m_y^2),  p = (gamma - 1)(E - ke/rho). */
+ * in, with zero slope).  For rho > 0 and gamma > 1, p = (gamma - 1)(E - ke/rho)
+ * is positive exactly when rho E - ke is; the test, in this fixed order:
+ *   ke = 0.5 (m_x^2 + m_y^2),  rho E - ke > 0. */
 static int nonphysical(int dim, double gam, const double* Q)
 {
+    (void)gam;
     double ke = dim == 2 ? 0.5 * (Q[1] * Q[1] + Q[2] * Q[2]) : 0.5 * (Q[1] * Q[1]);
-    double p = (gam - 1.0) * (Q[dim + 1] - ke / Q[0]);
-    return !(Q[0] > 0.0) || !(p > 0.0);
+    double pr = Q[dim + 1] * Q[0] - ke;
+    return !(Q[0] > 0.0) || !(pr > 0.0);
 }
 
 /* y = M x with the fixed summation order ((m0 x0 + m1 x1) + m2 x2) + m3 x3. */

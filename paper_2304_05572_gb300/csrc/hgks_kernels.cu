@@ -621,7 +621,7 @@ __device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const
     if (id >= n) return;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
     long long cell = g.origin + (long long)j * g.pitch + i;
-    const double inv_dx = 1.0 / g.dx, inv_dy = DIM == 2 ? 1.0 / g.dy : 0.0;
+    const double inv_dx = Sx.inv_hn, inv_dy = DIM == 2 ? Sy.inv_hn : 0.0;   // 1/dx, 1/dy (host-divided)
     long long perx = (long long)Sx.nt * Sx.nm, pery = DIM == 2 ? (long long)Sy.nt * Sy.nm : 0;
     long long ox = (long long)j * Sx.nm + i, oy = (long long)i * (DIM == 2 ? Sy.nm : 0) + j;
     double out[NV], acc[NV];
@@ -660,9 +660,10 @@ __device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const
         Wout[cell + (long long)k * g.plane] = out[k];
         if (STAGE == 0) Acc[cell + (long long)k * g.plane] = acc[k];
     }
-    double ke = DIM == 2 ? 0.5 * (out[1] * out[1] + out[2] * out[2]) / out[0] : 0.5 * out[1] * out[1] / out[0];
-    double p = (P.gamma - 1.0) * (out[NV - 1] - ke);
-    if (!(out[0] > 0.0) || !(p > 0.0) || !isfinite(out[0]) || !isfinite(p)) ctrl->status = HGKS_ENONPHYSICAL;
+    // rho > 0 and p > 0, the latter as rho E - |m|^2/2 > 0 (no division)
+    double ke = DIM == 2 ? 0.5 * fma(out[1], out[1], out[2] * out[2]) : 0.5 * out[1] * out[1];
+    double pr = fma(out[NV - 1], out[0], -ke);
+    if (!(out[0] > 0.0) || !(pr > 0.0) || !isfinite(out[0]) || !isfinite(pr)) ctrl->status = HGKS_ENONPHYSICAL;
 }
 
 template <int DIM, int STAGE>

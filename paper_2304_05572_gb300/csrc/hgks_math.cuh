@@ -251,15 +251,17 @@ __device__ __forceinline__ void weno_ao_face(double gam, const AOConst& k, const
 }
 
 // Reading (no safeguard is printed): rho <= 0 or p <= 0 after reconstruction -> first order.
-// ke = 0.5 (m_x^2 + m_y^2), p = (gamma-1)(E - ke/rho), in this order.
+// For rho > 0 (and gamma > 1), p > 0 exactly when rho E - ke > 0, ke = 0.5 (m_x^2 + m_y^2);
+// tested in that division-free form, in this order.
 template <int NV>
 __device__ __forceinline__ bool nonphysical(double gam, const double* Q)
 {
+    (void)gam;
     ex ke;
     if constexpr (NV == 4) ke = ex(0.5) * (ex(Q[1]) * ex(Q[1]) + ex(Q[2]) * ex(Q[2]));
     else ke = ex(0.5) * (ex(Q[1]) * ex(Q[1]));
-    ex p = (ex(gam) - ex(1.0)) * (ex(Q[NV - 1]) - ke / ex(Q[0]));
-    return !(Q[0] > 0.0) || !(p.v > 0.0);
+    ex pr = ex(Q[NV - 1]) * ex(Q[0]) - ke;
+    return !(Q[0] > 0.0) || !(pr.v > 0.0);
 }
 
 // ---------------------------------------------------------------- Gauss-point reconstruction
