@@ -40,15 +40,15 @@ WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS,
 
 # FP64 operations per Gauss-point flux evaluation of the 2D kernel with tau > 0, counted by
 # ncu as DADD + DMUL + 2 x DFMA thread instructions per Gauss point (512^2 four-quadrant
-# Riemann step; identical per Gauss point at any grid size): first stage 1710.6, second 1641.4.
-FLUX_FLOP_PER_GP_2D = (1710.6 + 1641.4) / 2
-# DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.1 and 114.2 MB first stage, 106.7
-# and 107.5 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
+# Riemann step; identical per Gauss point at any grid size): first stage 1696.6, second 1625.4.
+FLUX_FLOP_PER_GP_2D = (1696.6 + 1625.4) / 2
+# DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.2 and 113.7 MB first stage, 106.5
+# and 108.0 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
 # them: Gauss-point states in, per-Gauss-point fluxes out).
-FLUX_DRAM_BYTES_PER_GP = (113.1e6 + 114.2e6 + 106.7e6 + 107.5e6) / 4 / (2 * 512 * 513)
+FLUX_DRAM_BYTES_PER_GP = (113.15e6 + 113.74e6 + 106.53e6 + 108.01e6) / 4 / (2 * 512 * 513)
 # FP64 flop of one whole S2O4 step per cell-stage (all kernels, ncu DADD + DMUL + 2 x DFMA
 # over the 40 launches of one 512^2 four-quadrant step, troubled fraction 1.1 %).
-STEP_FLOP_PER_CELL_STAGE = 8855.0
+STEP_FLOP_PER_CELL_STAGE = 8569.7
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 

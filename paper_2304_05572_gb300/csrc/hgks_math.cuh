@@ -339,7 +339,8 @@ struct Mom {
 template <int DIM>
 struct MState {
     double rho, ri, U, V, p, h, lam, E;
-    double q, lam2c, two_lam;      // slope-solve constants: q = |U|^2 + Kq h, lam2c = lam^2 4/Kq
+    double q, lam2c, two_lam;      // slope-solve constants: q = |U|^2 + Kq h, lam2c = lam^2 (4/Kq)/rho,
+                                   // two_lam = 2 lam/rho (the 1/rho of <a> = dW/rho folded in)
 };
 
 struct FluxConst {
@@ -370,31 +371,32 @@ HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MS
     s.h = s.p * s.ri;
     s.lam = 0.5 / s.h;
     s.q = fma(s.U, s.U, fma(s.V, s.V, fc.Kq * s.h));
-    s.lam2c = s.lam * s.lam * fc.cslope;
-    s.two_lam = 2.0 * s.lam;
+    s.two_lam = 2.0 * s.lam * s.ri;
+    s.lam2c = s.lam * fc.cslope * (0.5 * s.two_lam);
     return s.rho > 0.0 && s.p > 0.0;
 }
 
-// Micro-slope a with <a> = b (b = dW/rho): closed-form inverse of the moment system of Eq. (8).
+// Micro-slope a with <a> = dW/rho: closed-form inverse of the moment system of Eq. (8), on the
+// unscaled derivative dW (the 1/rho is carried by lam2c, two_lam and the last line).
 template <int DIM>
-HGKS_HD __forceinline__ void slope_solve(const double* b, const MState<DIM>& s, double* a)
+HGKS_HD __forceinline__ void slope_solve(const double* dW, const MState<DIM>& s, double* a)
 {
     if constexpr (DIM == 2) {
-        double R4 = fma(-s.q, b[0], 2.0 * b[3]);
-        double R3 = fma(-s.V, b[0], b[2]);
-        double R2 = fma(-s.U, b[0], b[1]);
+        double R4 = fma(-s.q, dW[0], 2.0 * dW[3]);
+        double R3 = fma(-s.V, dW[0], dW[2]);
+        double R2 = fma(-s.U, dW[0], dW[1]);
         double a4 = s.lam2c * fma(-2.0 * s.V, R3, fma(-2.0 * s.U, R2, R4));
         double a3 = fma(-s.V, a4, s.two_lam * R3);
         double a2 = fma(-s.U, a4, s.two_lam * R2);
         a[3] = a4; a[2] = a3; a[1] = a2;
-        a[0] = fma(-0.5 * s.q, a4, fma(-s.V, a3, fma(-s.U, a2, b[0])));
+        a[0] = fma(-0.5 * s.q, a4, fma(-s.V, a3, fma(-s.U, a2, dW[0] * s.ri)));
     } else {
-        double R3 = fma(-s.q, b[0], 2.0 * b[2]);
-        double R2 = fma(-s.U, b[0], b[1]);
+        double R3 = fma(-s.q, dW[0], 2.0 * dW[2]);
+        double R2 = fma(-s.U, dW[0], dW[1]);
         double a3 = s.lam2c * fma(-2.0 * s.U, R2, R3);
         double a2 = fma(-s.U, a3, s.two_lam * R2);
         a[2] = a3; a[1] = a2;
-        a[0] = fma(-0.5 * s.q, a3, fma(-s.U, a2, b[0]));
+        a[0] = fma(-0.5 * s.q, a3, fma(-s.U, a2, dW[0] * s.ri));
     }
 }
 
@@ -660,20 +662,12 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     half_moments<DIM>(sr, -1, fc, mr);
 
     // micro-slopes of each side, Eq. (8)
-    double a1l[NV], a1r[NV], a2l[NV], a2r[NV], b[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) b[k] = Wlx[k] * sl.ri;
-    slope_solve<DIM>(b, sl, a1l);
-#pragma unroll
-    for (int k = 0; k < NV; k++) b[k] = Wrx[k] * sr.ri;
-    slope_solve<DIM>(b, sr, a1r);
+    double a1l[NV], a1r[NV], a2l[NV], a2r[NV];
+    slope_solve<DIM>(Wlx, sl, a1l);
+    slope_solve<DIM>(Wrx, sr, a1r);
     if constexpr (DIM == 2) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = Wly[k] * sl.ri;
-        slope_solve<DIM>(b, sl, a2l);
-#pragma unroll
-        for (int k = 0; k < NV; k++) b[k] = Wry[k] * sr.ri;
-        slope_solve<DIM>(b, sr, a2r);
+        slope_solve<DIM>(Wly, sl, a2l);
+        slope_solve<DIM>(Wry, sr, a2r);
     }
 
     // equilibrium state and its slopes by kinetic weighting, Eqs. (46)-(47)
@@ -784,9 +778,7 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
             const double* L4 = side == 0 ? pl1 : pr1;
             double Wt[NV], As[NV], L5[NV], L6[NV];
             w_t<DIM>(st, side == 0 ? Wlx : Wrx, side == 0 ? Wly : Wry, fc.gm1, Wt);
-#pragma unroll
-            for (int k = 0; k < NV; k++) b[k] = Wt[k] * st.ri;
-            slope_solve<DIM>(b, st, As);
+            slope_solve<DIM>(Wt, st, As);
             Gm<DIM, 2, 0>(a1, mh, L5);
             if constexpr (DIM == 2) {
                 Gm<DIM, 1, 1>(a2, mh, t1);
