@@ -6,16 +6,20 @@ device memory its solver needs (hgks_footprint_bytes) fits in the budget;
 admitted solves keep their state resident on the device and advance together:
 every iteration issues one batched group of S2O4 steps (hgks_batch_step, CUDA
 graph replay) per dimension for all resident solves, the 1D and 2D groups on
-their own streams so that they overlap on the device, so newly admitted solves
-overlap on the device with the ones already running.  A solve retires at its
-end time (or when its state turned non-physical: the scheme has no positivity
-limiter, and the status is reported with the result); its state is copied
-back, its memory freed and its latency (completion minus arrival, queueing
-included) recorded.
+their own streams so that they overlap on the device, and newly admitted solves
+join the ones already running.  A solve retires at its end time, when its
+state turned non-physical (the scheme has no positivity limiter; the status is
+reported with the result) or when its request is cancelled; its state is
+copied back, its memory freed and its latency (completion minus arrival,
+queueing included) recorded.  A request whose configuration the library
+rejects, or whose memory alone exceeds the budget, is answered at once with a
+"rejected" status and takes no device memory.
 
 Each solve's arithmetic is independent of the others (batched launches never
 mix solvers inside a block), so a result is bit-identical alone and in the mix.
-All numerical work runs in the CUDA library; this module only schedules.
+All numerical work runs in the CUDA library; this module only schedules, over a
+small backend interface (GpuBackend here; the scheduling logic is the same for
+any object with its methods).
 """
 from __future__ import annotations
 
@@ -25,99 +29,158 @@ import numpy as np
 
 from . import hgks
 
+STATUS_OK = 0
+STATUS_NONPHYSICAL = hgks.HGKS_ENONPHYSICAL
+STATUS_REJECTED = "rejected"
+STATUS_CANCELLED = "cancelled"
 
-class Server:
-    def __init__(self, budget_bytes: float, stream=None, steps_per_iter: int = 4, autotune: bool = False):
+
+class GpuBackend:
+    """Solvers on the current CUDA device, advanced by one hgks batch per dimension."""
+
+    def __init__(self, stream=None, autotune: bool = False):
         import torch
-        self.budget = float(budget_bytes)
         # one stream per dimension: the 1D batch (small, latency-bound launches) overlaps on the
         # device with the 2D batch; `stream`, if given, serves the 2D solves
         self.streams = {1: torch.cuda.Stream(), 2: stream if stream is not None else torch.cuda.Stream()}
-        self.steps_per_iter = int(steps_per_iter)
         self.autotune = autotune
-        self.used = 0.0
-        self.active = {}          # id -> dict(req, solver, bytes, t_admit)
-        self.results = {}         # id -> dict(W, latency, admitted, completed, steps, t, status, cells)
-        self._batches = {}        # dim -> (tuple of ids, Batch)
-        self.iterations = 0
-        self.peak_resident = 0
+        self._batches = {}        # dim -> (tuple of handles, Batch)
 
-    def _admit(self, req, now):
-        dim = int(req["cfg"]["dim"])
-        s = hgks.Solver(req["cfg"], stream=self.streams[dim])
-        s.hgks_set_state(np.ascontiguousarray(req["W"]))
-        self.active[req["id"]] = dict(req=req, solver=s, bytes=req["bytes"], t_admit=now)
-        self.used += req["bytes"]
-        self.peak_resident = max(self.peak_resident, len(self.active))
+    def footprint(self, cfg) -> int:
+        """Device bytes of a solver of cfg; 0 if the library rejects the configuration."""
+        try:
+            return int(hgks.hgks_footprint_bytes(cfg))
+        except (KeyError, TypeError, ValueError):
+            return 0
 
-    def _retire(self, rid, now, t, status, steps):
-        a = self.active.pop(rid)
-        s = a["solver"]
-        self.results[rid] = dict(W=s.hgks_get_state(), latency=now - a["req"]["arrival"], admitted=a["t_admit"],
-                                 completed=now, steps=int(steps), t=t, status=int(status),
-                                 cells=int(np.prod(a["req"]["W"].shape[1:])))
-        s.hgks_destroy_solver()
-        self.used -= a["bytes"]
+    def create(self, cfg, W):
+        s = hgks.Solver(cfg, stream=self.streams[int(cfg["dim"])])
+        s.hgks_set_state(np.ascontiguousarray(W))
+        return s
 
-    def _batch_for(self, dim, ids):
-        key = tuple(sorted(ids))
+    def _batch(self, dim, handles):
+        key = tuple(handles)
         cur = self._batches.get(dim)
         if cur is not None and cur[0] == key:
             return cur[1]
         if cur is not None:
             cur[1].hgks_batch_destroy()
-        b = hgks.Batch([self.active[i]["solver"] for i in key], stream=self.streams[dim])
+        b = hgks.Batch(list(key), stream=self.streams[dim])
         self._batches[dim] = (key, b)
         return b
 
+    def step(self, dim, handles, t_ends, nsteps):
+        """Enqueue nsteps batched steps of the given solvers (no wait)."""
+        self._batch(dim, handles).hgks_batch_step(t_ends, nsteps=nsteps, graph=True, autotune=self.autotune)
+
+    def sync(self, dim):
+        """Wait for the dimension's batch; (t, status, steps) per solver in step() order."""
+        b = self._batches[dim][1]
+        b.hgks_batch_sync()
+        return list(zip(*b.hgks_batch_status()))
+
+    def fetch(self, handle):
+        return handle.hgks_get_state()
+
+    def release(self, handle):
+        handle.hgks_destroy_solver()
+
+    def close(self):
+        for _, b in self._batches.values():
+            b.hgks_batch_destroy()
+        self._batches.clear()
+
+
+class Server:
+    def __init__(self, budget_bytes: float, stream=None, steps_per_iter: int = 4, autotune: bool = False,
+                 backend=None, clock=time.perf_counter):
+        self.budget = float(budget_bytes)
+        self.backend = backend if backend is not None else GpuBackend(stream, autotune)
+        self.steps_per_iter = int(steps_per_iter)
+        self.clock = clock
+        self.used = 0.0
+        self.active = {}          # id -> dict(req, handle, bytes, t_admit)
+        self.results = {}         # id -> dict(W, latency, admitted, completed, steps, t, status, cells)
+        self.iterations = 0
+        self.peak_resident = 0
+
+    def _admit(self, req, now):
+        h = self.backend.create(req["cfg"], req["W"])
+        self.active[req["id"]] = dict(req=req, handle=h, bytes=req["bytes"], t_admit=now)
+        self.used += req["bytes"]
+        self.peak_resident = max(self.peak_resident, len(self.active))
+
+    def _answer(self, req, now, status, W=None, t=0.0, steps=0, admitted=None):
+        self.results[req["id"]] = dict(W=W, latency=now - req["arrival"], admitted=admitted, completed=now,
+                                       steps=int(steps), t=t, status=status,
+                                       cells=int(np.prod(np.shape(req["W"])[1:])))
+
+    def _retire(self, rid, now, t, status, steps):
+        a = self.active.pop(rid)
+        W = self.backend.fetch(a["handle"])
+        self.backend.release(a["handle"])
+        self.used -= a["bytes"]
+        self._answer(a["req"], now, status, W=W, t=t, steps=steps, admitted=a["t_admit"])
+
     def run(self, trace, time_scale: float = 1.0):
-        """Serve a list of requests (dicts with id, arrival [s], cfg, W, t_end) in arrival
-        order; arrival times are scaled by time_scale.  Returns the results dict."""
-        pending = sorted(({**r, "arrival": r["arrival"] * time_scale,
-                           "bytes": float(hgks.hgks_footprint_bytes(r["cfg"]))} for r in trace),
-                         key=lambda r: r["arrival"])
-        for r in pending:
-            if r["bytes"] > self.budget:
-                raise ValueError("request %d alone exceeds the memory budget" % r["id"])
-        t0 = time.perf_counter()
+        """Serve a list of requests (dicts with id, arrival [s], cfg, W, t_end and optionally
+        cancel_at [s]) in arrival order; times are scaled by time_scale.  Returns the results
+        dict, one entry per request."""
+        pending = []
+        for r in sorted(trace, key=lambda r: r["arrival"]):
+            q = dict(r, arrival=r["arrival"] * time_scale)
+            if r.get("cancel_at") is not None:
+                q["cancel_at"] = r["cancel_at"] * time_scale
+            q["bytes"] = float(self.backend.footprint(r["cfg"]))
+            pending.append(q)
+        t0 = self.clock()
         qi = 0
         while qi < len(pending) or self.active:
-            now = time.perf_counter() - t0
-            while qi < len(pending) and pending[qi]["arrival"] <= now and self.used + pending[qi]["bytes"] <= self.budget:
-                self._admit(pending[qi], now)
+            now = self.clock() - t0
+            # admission in arrival order (FIFO): a request that cannot fit waits, and so do the ones behind it
+            while qi < len(pending) and pending[qi]["arrival"] <= now:
+                req = pending[qi]
+                if not (req["bytes"] > 0 and req["bytes"] <= self.budget):
+                    self._answer(req, now, STATUS_REJECTED)       # invalid, or larger than the whole budget
+                    qi += 1
+                    continue
+                if req.get("cancel_at") is not None and req["cancel_at"] <= now:
+                    self._answer(req, now, STATUS_CANCELLED)      # cancelled while queued
+                    qi += 1
+                    continue
+                if self.used + req["bytes"] > self.budget:
+                    break
+                self._admit(req, now)
                 qi += 1
+            for rid in [rid for rid, a in self.active.items()
+                        if a["req"].get("cancel_at") is not None and a["req"]["cancel_at"] <= now]:
+                self._retire(rid, now, None, STATUS_CANCELLED, 0)
             if not self.active:
                 if qi < len(pending):
-                    time.sleep(max(0.0, min(0.01, pending[qi]["arrival"] - now)))
+                    wait = pending[qi]["arrival"] - now
+                    if wait > 0:
+                        time.sleep(min(0.01, wait))
                 continue
             by_dim = {}
             for rid, a in self.active.items():
                 by_dim.setdefault(int(a["req"]["cfg"]["dim"]), []).append(rid)
-            stepped = []
             for dim, ids in by_dim.items():             # enqueue every dimension first (they overlap)
-                b = self._batch_for(dim, ids)
-                key = self._batches[dim][0]
-                b.hgks_batch_step([self.active[i]["req"]["t_end"] for i in key], nsteps=self.steps_per_iter,
-                                  graph=True, autotune=self.autotune)
-                stepped.append(dim)
+                ids.sort()
+                self.backend.step(dim, [self.active[i]["handle"] for i in ids],
+                                  [self.active[i]["req"]["t_end"] for i in ids], self.steps_per_iter)
             self.iterations += 1
             finished = []
-            for dim in stepped:
-                key, b = self._batches[dim]
-                b.hgks_batch_sync()
-                ts, sts, nsteps = b.hgks_batch_status()
-                for rid, t, st, n in zip(key, ts, sts, nsteps):
+            for dim, ids in by_dim.items():
+                for rid, (t, st, n) in zip(ids, self.backend.sync(dim)):
                     te = self.active[rid]["req"]["t_end"]
                     # a solve retires at its end time, or with its error once its state turned non-physical
                     if st != 0 or te - t <= 1e-12 * max(1.0, abs(te)):
                         finished.append((rid, t, st, n))
-            now = time.perf_counter() - t0
+            now = self.clock() - t0
             for rid, t, st, n in finished:
                 self._retire(rid, now, t, st, n)
-        for dim, (key, b) in list(self._batches.items()):
-            b.hgks_batch_destroy()
-        self._batches.clear()
-        self.wall = time.perf_counter() - t0
+        self.backend.close()
+        self.wall = self.clock() - t0
         return self.results
 
 
