@@ -361,7 +361,8 @@ def bench_recon_cost(args, torch, hgks, P):
             total = sum(v[0] for v in tim.values())
             troubled = float(st["troubled"].sum()) / max(1, int(st["examined"].sum()))
             res[mode] = dict(recon_ms=recon, kernel_ms=total, wall_s=wall, steps=int(st["steps"]),
-                             t=st["t"], status=int(st["status"]), troubled_fraction=troubled)
+                             t=st["t"], status=int(st["status"]), troubled_fraction=troubled,
+                             class_ms={k: round(v[0], 3) for k, v in tim.items() if v[1]})
         paper = PAPER_RECON_S.get(name)
         rows.append(dict(case=name, cells=int(np.prod(W.shape[1:])), hybrid=res["hybrid"], wenoao=res["wenoao"],
                          recon_ratio=res["hybrid"]["recon_ms"] / max(1e-9, res["wenoao"]["recon_ms"]),

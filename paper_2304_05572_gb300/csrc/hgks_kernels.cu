@@ -503,26 +503,27 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
         int X = it & 3;
         long long tm = it >> 2;
         int m = (int)(tm % S.nm), t = (int)(tm / S.nm);
-        ex qs[4], Lm[4][4], Rm[4][4], Uc[5][4];
+        // tangential outputs feed only the flux: free-order arithmetic (fx), FMA contraction allowed
+        fx qs[4], Lm[4][4], Rm[4][4], Uc[5][4];
         const double* cl = cellp(P, S, W, t, m - 1);
         const double* cr = cellp(P, S, W, t, m);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             long long o = (long long)S.perm[k] * P.g.plane;
-            qs[k] = (ex(ld(cl + o)) + ex(ld(cr + o))) * ex(0.5);
+            qs[k] = (fx(ld(cl + o)) + fx(ld(cr + o))) * fx(0.5);
         }
         eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
 #pragma unroll
         for (int s = 0; s < 5; s++) {
-            ex x[4];
+            fx x[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) x[k] = ex(lineval(S, X, k, t - 2 + s, m));
+            for (int k = 0; k < 4; k++) x[k] = fx(lineval(S, X, k, t - 2 + s, m));
             matvec<4>(Lm, x, Uc[s]);
         }
         double cv[4][2], cd[4][2];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            ex q[5];
+            fx q[5];
 #pragma unroll
             for (int s = 0; s < 5; s++) q[s] = Uc[s][k];
             gauss_ao(q, ak, cv[k], cd[k]);

@@ -39,6 +39,25 @@ __device__ __forceinline__ ex xfma(ex a, ex b, ex c) { return ex(__fma_rn(a.v, b
 __device__ __forceinline__ ex xabs(ex a) { return ex(fabs(a.v)); }
 __device__ __forceinline__ ex xsqrt(ex a) { return ex(__dsqrt_rn(a.v)); }
 
+// Free-order FP64 with the same interface: the compiler may contract a*b + c into an FMA.  Used
+// where the outputs only feed the flux (the tangential WENO-AO pass), never a flag decision.
+struct fx {
+    double v;
+    __device__ __forceinline__ fx() {}
+    __device__ __forceinline__ fx(double x) : v(x) {}
+};
+__device__ __forceinline__ fx operator+(fx a, fx b) { return fx(a.v + b.v); }
+__device__ __forceinline__ fx operator-(fx a, fx b) { return fx(a.v - b.v); }
+__device__ __forceinline__ fx operator*(fx a, fx b) { return fx(a.v * b.v); }
+__device__ __forceinline__ fx operator/(fx a, fx b) { return fx(a.v / b.v); }
+__device__ __forceinline__ fx operator-(fx a) { return fx(-a.v); }
+__device__ __forceinline__ fx xfma(fx a, fx b, fx c) { return fx(fma(a.v, b.v, c.v)); }
+__device__ __forceinline__ fx xabs(fx a) { return fx(fabs(a.v)); }
+__device__ __forceinline__ fx xsqrt(fx a) { return fx(sqrt(a.v)); }
+
+template <typename T> struct exact_order { static constexpr bool value = false; };
+template <> struct exact_order<ex> { static constexpr bool value = true; };
+
 // Troubled-cell indicator, Sec. 2.3.1 Steps 1-3, on the window q[0..4] = Q_{i-2..i+2}
 // (cell units).  Step 1: |D| <= Z1 with D = (4Q_{i-2}+Q_{i-1}) + (4Q_{i+2}+Q_{i+1}) - 10 Q_i
 // and Z1 = 17 zeta1 dx^2 (Eq. (24): abar2 = D/34).  Step 2: xbar = -abar1/(2 abar2) with
@@ -98,35 +117,52 @@ struct AOConst {
     double eps;
 };
 
-// Smoothness indicators of Eq. (39) in cell units (same evaluation order as the decisions need).
-__device__ __forceinline__ void ao_betas(const ex* q, ex* b)
+// Smoothness indicators of Eq. (39) in cell units (with T = ex: the evaluation order the
+// decisions need).
+template <typename T>
+__device__ __forceinline__ void ao_betas(const T* q, T* b)
 {
-    ex s0 = (q[0] - ex(2.0) * q[1]) + q[2], t0 = (q[0] - ex(4.0) * q[1]) + ex(3.0) * q[2];
-    ex s1 = (q[1] - ex(2.0) * q[2]) + q[3], t1 = q[1] - q[3];
-    ex s2 = (q[2] - ex(2.0) * q[3]) + q[4], t2 = (ex(3.0) * q[2] - ex(4.0) * q[3]) + q[4];
-    b[0] = ex(13.0 / 12.0) * (s0 * s0) + ex(0.25) * (t0 * t0);
-    b[1] = ex(13.0 / 12.0) * (s1 * s1) + ex(0.25) * (t1 * t1);
-    b[2] = ex(13.0 / 12.0) * (s2 * s2) + ex(0.25) * (t2 * t2);
-    ex c1 = ex(17.0 / 24.0) * (q[3] - q[1]) - ex(5.0 / 48.0) * (q[4] - q[0]);
-    ex c2 = ((ex(0.75) * (q[1] + q[3]) - ex(0.0625) * (q[0] + q[4])) - ex(1.375) * q[2]);
-    ex c3 = ex(1.0 / 6.0) * (q[1] - q[3]) - ex(1.0 / 12.0) * (q[0] - q[4]);
-    ex c4 = ((ex(1.0 / 24.0) * (q[0] + q[4]) - ex(1.0 / 6.0) * (q[1] + q[3])) + ex(0.25) * q[2]);
-    b[3] = ((((c1 * c1 + ex(0.5) * (c1 * c3)) + ex(13.0 / 3.0) * (c2 * c2)) + ex(21.0 / 5.0) * (c2 * c4))
-            + ex(3129.0 / 80.0) * (c3 * c3)) + ex(87617.0 / 140.0) * (c4 * c4);
+    T s0 = (q[0] - T(2.0) * q[1]) + q[2], t0 = (q[0] - T(4.0) * q[1]) + T(3.0) * q[2];
+    T s1 = (q[1] - T(2.0) * q[2]) + q[3], t1 = q[1] - q[3];
+    T s2 = (q[2] - T(2.0) * q[3]) + q[4], t2 = (T(3.0) * q[2] - T(4.0) * q[3]) + q[4];
+    b[0] = T(13.0 / 12.0) * (s0 * s0) + T(0.25) * (t0 * t0);
+    b[1] = T(13.0 / 12.0) * (s1 * s1) + T(0.25) * (t1 * t1);
+    b[2] = T(13.0 / 12.0) * (s2 * s2) + T(0.25) * (t2 * t2);
+    T c1 = T(17.0 / 24.0) * (q[3] - q[1]) - T(5.0 / 48.0) * (q[4] - q[0]);
+    T c2 = ((T(0.75) * (q[1] + q[3]) - T(0.0625) * (q[0] + q[4])) - T(1.375) * q[2]);
+    T c3 = T(1.0 / 6.0) * (q[1] - q[3]) - T(1.0 / 12.0) * (q[0] - q[4]);
+    T c4 = ((T(1.0 / 24.0) * (q[0] + q[4]) - T(1.0 / 6.0) * (q[1] + q[3])) + T(0.25) * q[2]);
+    b[3] = ((((c1 * c1 + T(0.5) * (c1 * c3)) + T(13.0 / 3.0) * (c2 * c2)) + T(21.0 / 5.0) * (c2 * c4))
+            + T(3129.0 / 80.0) * (c3 * c3)) + T(87617.0 / 140.0) * (c4 * c4);
 }
 
 // Normalised nonlinear weights, Eqs. (37), (38), (40), with the ratio delta/(beta_k + eps) squared.
-__device__ __forceinline__ void ao_weights(const ex* q, const AOConst& k, ex* wb)
+// With T = fx the four ratios share one division (1/(e0 e1 e2 e3) times the other three factors)
+// whenever that product is a finite positive number.
+template <typename T>
+__device__ __forceinline__ void ao_weights(const T* q, const AOConst& k, T* wb)
 {
-    ex b[4], w[4];
+    T b[4], w[4], r[4];
     ao_betas(q, b);
-    ex d = ((xabs(b[3] - b[0]) + xabs(b[3] - b[1])) + xabs(b[3] - b[2])) * ex(1.0 / 3.0);
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        ex r = d / (b[j] + ex(k.eps));
-        w[j] = ex(k.g[j]) * (ex(1.0) + r * r);
+    T d = ((xabs(b[3] - b[0]) + xabs(b[3] - b[1])) + xabs(b[3] - b[2])) * T(1.0 / 3.0);
+    bool done = false;
+    if constexpr (!exact_order<T>::value) {
+        const double e0 = b[0].v + k.eps, e1 = b[1].v + k.eps, e2 = b[2].v + k.eps, e3 = b[3].v + k.eps;
+        const double e01 = e0 * e1, e23 = e2 * e3, prod = e01 * e23;
+        if (prod > 0.0 && prod < 1e300) {
+            const double di = d.v / prod;
+            r[0] = T(di * (e1 * e23)); r[1] = T(di * (e0 * e23));
+            r[2] = T(di * (e3 * e01)); r[3] = T(di * (e2 * e01));
+            done = true;
+        }
     }
-    ex inv = ex(1.0) / (((w[0] + w[1]) + w[2]) + w[3]);
+    if (!done) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) r[j] = d / (b[j] + T(k.eps));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) w[j] = T(k.g[j]) * (T(1.0) + r[j] * r[j]);
+    T inv = T(1.0) / (((w[0] + w[1]) + w[2]) + w[3]);
 #pragma unroll
     for (int j = 0; j < 4; j++) wb[j] = w[j] * inv;
 }
@@ -164,51 +200,51 @@ __device__ __forceinline__ void face_polys(const ex* q, int side, ex* pv, ex* pd
 }
 
 // Left (L = R^{-1}, rows) and right (R, columns) eigenvectors of nx dF/dQ + ny dG/dQ at Q.
-template <int NV>
-__device__ __forceinline__ void eigvec(double gam, const ex* Q, double nxd, double nyd, ex (*L)[NV], ex (*R)[NV])
+template <int NV, typename T>
+__device__ __forceinline__ void eigvec(double gam, const T* Q, double nxd, double nyd, T (*L)[NV], T (*R)[NV])
 {
-    ex gm1 = ex(gam) - ex(1.0);
-    ex rho = Q[0], ri = ex(1.0) / rho;
-    ex U = Q[1] * ri;
+    T gm1 = T(gam) - T(1.0);
+    T rho = Q[0], ri = T(1.0) / rho;
+    T U = Q[1] * ri;
     if constexpr (NV == 4) {
-        ex nx(nxd), ny(nyd);
-        ex V = Q[2] * ri;
-        ex q2 = U * U + V * V;
-        ex p = gm1 * (Q[3] - (ex(0.5) * rho) * q2);
-        ex c2 = (ex(gam) * p) * ri, c = xsqrt(c2), ci = ex(1.0) / c;
-        ex H = (Q[3] + p) * ri;
-        ex un = U * nx + V * ny, ut = V * nx - U * ny;
-        ex b1 = gm1 / c2, b2 = (ex(0.5) * b1) * q2;
-        R[0][0] = ex(1.0);    R[0][1] = ex(1.0);       R[0][2] = ex(0.0); R[0][3] = ex(1.0);
+        T nx(nxd), ny(nyd);
+        T V = Q[2] * ri;
+        T q2 = U * U + V * V;
+        T p = gm1 * (Q[3] - (T(0.5) * rho) * q2);
+        T c2 = (T(gam) * p) * ri, c = xsqrt(c2), ci = T(1.0) / c;
+        T H = (Q[3] + p) * ri;
+        T un = U * nx + V * ny, ut = V * nx - U * ny;
+        T b1 = gm1 / c2, b2 = (T(0.5) * b1) * q2;
+        R[0][0] = T(1.0);    R[0][1] = T(1.0);       R[0][2] = T(0.0); R[0][3] = T(1.0);
         R[1][0] = U - c * nx; R[1][1] = U;             R[1][2] = -ny;     R[1][3] = U + c * nx;
         R[2][0] = V - c * ny; R[2][1] = V;             R[2][2] = nx;      R[2][3] = V + c * ny;
-        R[3][0] = H - un * c; R[3][1] = ex(0.5) * q2;  R[3][2] = ut;      R[3][3] = H + un * c;
-        L[0][0] = ex(0.5) * (b2 + un * ci); L[0][1] = -(ex(0.5) * (b1 * U + nx * ci)); L[0][2] = -(ex(0.5) * (b1 * V + ny * ci)); L[0][3] = ex(0.5) * b1;
-        L[1][0] = ex(1.0) - b2;             L[1][1] = b1 * U;                          L[1][2] = b1 * V;                          L[1][3] = -b1;
-        L[2][0] = -ut;                      L[2][1] = -ny;                             L[2][2] = nx;                              L[2][3] = ex(0.0);
-        L[3][0] = ex(0.5) * (b2 - un * ci); L[3][1] = -(ex(0.5) * (b1 * U - nx * ci)); L[3][2] = -(ex(0.5) * (b1 * V - ny * ci)); L[3][3] = ex(0.5) * b1;
+        R[3][0] = H - un * c; R[3][1] = T(0.5) * q2;  R[3][2] = ut;      R[3][3] = H + un * c;
+        L[0][0] = T(0.5) * (b2 + un * ci); L[0][1] = -(T(0.5) * (b1 * U + nx * ci)); L[0][2] = -(T(0.5) * (b1 * V + ny * ci)); L[0][3] = T(0.5) * b1;
+        L[1][0] = T(1.0) - b2;             L[1][1] = b1 * U;                          L[1][2] = b1 * V;                          L[1][3] = -b1;
+        L[2][0] = -ut;                      L[2][1] = -ny;                             L[2][2] = nx;                              L[2][3] = T(0.0);
+        L[3][0] = T(0.5) * (b2 - un * ci); L[3][1] = -(T(0.5) * (b1 * U - nx * ci)); L[3][2] = -(T(0.5) * (b1 * V - ny * ci)); L[3][3] = T(0.5) * b1;
     } else {
-        ex q2 = U * U;
-        ex p = gm1 * (Q[2] - (ex(0.5) * rho) * q2);
-        ex c2 = (ex(gam) * p) * ri, c = xsqrt(c2), ci = ex(1.0) / c;
-        ex H = (Q[2] + p) * ri;
-        ex b1 = gm1 / c2, b2 = (ex(0.5) * b1) * q2;
-        R[0][0] = ex(1.0);    R[0][1] = ex(1.0);      R[0][2] = ex(1.0);
+        T q2 = U * U;
+        T p = gm1 * (Q[2] - (T(0.5) * rho) * q2);
+        T c2 = (T(gam) * p) * ri, c = xsqrt(c2), ci = T(1.0) / c;
+        T H = (Q[2] + p) * ri;
+        T b1 = gm1 / c2, b2 = (T(0.5) * b1) * q2;
+        R[0][0] = T(1.0);    R[0][1] = T(1.0);      R[0][2] = T(1.0);
         R[1][0] = U - c;      R[1][1] = U;            R[1][2] = U + c;
-        R[2][0] = H - U * c;  R[2][1] = ex(0.5) * q2; R[2][2] = H + U * c;
-        L[0][0] = ex(0.5) * (b2 + U * ci); L[0][1] = -(ex(0.5) * (b1 * U + ci)); L[0][2] = ex(0.5) * b1;
-        L[1][0] = ex(1.0) - b2;            L[1][1] = b1 * U;                     L[1][2] = -b1;
-        L[2][0] = ex(0.5) * (b2 - U * ci); L[2][1] = -(ex(0.5) * (b1 * U - ci)); L[2][2] = ex(0.5) * b1;
+        R[2][0] = H - U * c;  R[2][1] = T(0.5) * q2; R[2][2] = H + U * c;
+        L[0][0] = T(0.5) * (b2 + U * ci); L[0][1] = -(T(0.5) * (b1 * U + ci)); L[0][2] = T(0.5) * b1;
+        L[1][0] = T(1.0) - b2;            L[1][1] = b1 * U;                     L[1][2] = -b1;
+        L[2][0] = T(0.5) * (b2 - U * ci); L[2][1] = -(T(0.5) * (b1 * U - ci)); L[2][2] = T(0.5) * b1;
     }
 }
 
 // y = M x with the summation order ((m0 x0 + m1 x1) + m2 x2) + m3 x3.
-template <int NV>
-__device__ __forceinline__ void matvec(const ex (*M)[NV], const ex* x, ex* y)
+template <int NV, typename T>
+__device__ __forceinline__ void matvec(const T (*M)[NV], const T* x, T* y)
 {
 #pragma unroll
     for (int r = 0; r < NV; r++) {
-        ex s = M[r][0] * x[0] + M[r][1] * x[1];
+        T s = M[r][0] * x[0] + M[r][1] * x[1];
 #pragma unroll
         for (int c = 2; c < NV; c++) s = s + M[r][c] * x[c];
         y[r] = s;
@@ -302,9 +338,9 @@ __device__ __forceinline__ void gauss_linear(const double* q, double* v, double*
     v[0] = a; v[1] = b; d[0] = e; d[1] = f;
 }
 
-__device__ __forceinline__ void gauss_ao(const ex* q, const AOConst& k, double* v, double* d)
+__device__ __forceinline__ void gauss_ao(const fx* q, const AOConst& k, double* v, double* d)
 {
-    ex wb[4];
+    fx wb[4];
     ao_weights(q, k, wb);
     double w3 = wb[3].v * k.g3inv;
     // weight of each polynomial in the AO combination (Eq. (41)):
