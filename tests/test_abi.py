@@ -57,6 +57,7 @@ def test_config_default_layout(L):
     (dict(bc=["periodic", "extrap", "extrap", "extrap"]), "periodic"),
     (dict(recon_mode=7), "recon"),
     (dict(gamma_hi=1.0), "gamma_hi"),
+    (dict(nx=20000, ny=20000), "too large"),
 ])
 def test_invalid_config_rejected_before_device_work(L, bad, msg):
     cfg = dict(dim=2, nx=16, ny=16, x0=0.0, x1=1.0, y0=0.0, y1=1.0)

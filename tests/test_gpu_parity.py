@@ -218,9 +218,17 @@ def test_free_stream_bitwise_and_conservation():
 # ------------------------------------------------------------------ full size (benchmark configuration)
 
 def test_riemann4_1024_full_size_step():
-    """One step of the 1024^2 benchmark configuration, whole grid against the oracle."""
+    """The 1024^2 benchmark configuration through the solver path the benchmark times: the
+    first step, and the 11th step from the GPU's own state after 10 steps, whole grid
+    against the oracle."""
     cfg, W, _ = P.riemann4_2d(1024)
     check_step(cfg, W, "1024^2")
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(W)
+    assert s.hgks_step(1e9, 10) == 10
+    W10, t10 = s.hgks_get_state(), s.hgks_get_time()
+    s.hgks_destroy_solver()
+    check_step(cfg, W10, "1024^2 step 11", t0=t10)
 
 
 # ------------------------------------------------------------------ API behaviour
