@@ -40,12 +40,12 @@ WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS,
 
 # FP64 operations per Gauss-point flux evaluation of the 2D kernel with tau > 0, counted by
 # ncu as DADD + DMUL + 2 x DFMA thread instructions per Gauss point (512^2 four-quadrant
-# Riemann step; identical per Gauss point at any grid size): first stage 1696.6, second 1625.4.
-FLUX_FLOP_PER_GP_2D = (1696.6 + 1625.4) / 2
-# DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.2 and 113.7 MB first stage, 106.5
-# and 108.0 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
+# Riemann step; identical per Gauss point at any grid size): first stage 1665.6, second 1616.4.
+FLUX_FLOP_PER_GP_2D = (1665.6 + 1616.4) / 2
+# DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.0 and 113.8 MB first stage, 106.9
+# and 107.8 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
 # them: Gauss-point states in, per-Gauss-point fluxes out).
-FLUX_DRAM_BYTES_PER_GP = (113.15e6 + 113.74e6 + 106.53e6 + 108.01e6) / 4 / (2 * 512 * 513)
+FLUX_DRAM_BYTES_PER_GP = (113.03e6 + 113.80e6 + 106.85e6 + 107.77e6) / 4 / (2 * 512 * 513)
 # FP64 flop of one whole S2O4 step per cell-stage (all kernels, ncu DADD + DMUL + 2 x DFMA
 # over the 40 launches of one 512^2 four-quadrant step, troubled fraction 1.1 %).
 STEP_FLOP_PER_CELL_STAGE = 8569.7

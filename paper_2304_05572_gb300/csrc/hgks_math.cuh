@@ -362,8 +362,8 @@ __device__ __forceinline__ void gauss_ao(const fx* q, const AOConst& k, double* 
 }
 
 // ---------------------------------------------------------------- gas-kinetic flux
-// Normalised moments of a Maxwellian: u^n (full or one half line, n <= 6), v^m (full, m <= 5),
-// xi^2, xi^4.  Powers beyond these are never contracted.
+// Moments of a Maxwellian: u^n on one half line times the density (n <= 6), normalised v^m
+// (full line, m <= 5), xi^2, xi^4.  Powers beyond these are never contracted.
 template <int DIM>
 struct Mom {
     double u[7];
@@ -605,15 +605,6 @@ HGKS_HD __forceinline__ void recur_u(const MState<DIM>& s, Mom<DIM>& m)
     for (int n = 0; n < 5; n++) m.u[n + 2] = fma(s.U, m.u[n + 1], ((double)(n + 1) * s.h) * m.u[n]);
 }
 
-template <int DIM>
-HGKS_HD __forceinline__ void full_moments(const MState<DIM>& s, const FluxConst& fc, Mom<DIM>& m)
-{
-    m.u[0] = 1.0;
-    m.u[1] = s.U;
-    recur_u<DIM>(s, m);
-    fill_vx<DIM>(s, fc, m);
-}
-
 #include "erfcx_table.inc"
 
 // erfcx(y) = exp(y^2) erfc(y) on [0, 8): per interval [k/4, (k+1)/4) a degree-11 polynomial in
@@ -645,7 +636,9 @@ HGKS_HD __forceinline__ double erfc_nonneg(double y, double ey)
 }
 
 // Half-line moments of the left state over u > 0 (sign = +1) or of the right state over
-// u < 0 (sign = -1): <1> = erfc(-+sqrt(lam) U)/2, <u> = U <1> +- exp(-lam U^2)/(2 sqrt(pi lam)).
+// u < 0 (sign = -1), carrying the density: u[n] = rho <u^n> on the half line, with
+// <1> = erfc(-+sqrt(lam) U)/2, <u> = U <1> +- exp(-lam U^2)/(2 sqrt(pi lam)).  Every moment
+// product formed from them (psi_mom, Gm) has exactly one u-factor and so carries rho too.
 // With x = sqrt(lam) U, erfc(-+x) is formed from E = erfc(|x|): the half line that the mean
 // velocity points into holds 1 - E/2 of the mass, the other E/2.
 template <int DIM>
@@ -654,10 +647,11 @@ HGKS_HD __forceinline__ void half_moments(const MState<DIM>& s, int sign, const 
     const double sl = sqrt(s.lam);
     const double x = sl * s.U;
     const double ex2 = exp(-x * x);
-    const double e = ex2 * (0.56418958354775628695 * s.h * sl);   // 1/sqrt(pi) h sqrt(lam)
+    const double e = ex2 * (0.56418958354775628695 * s.p * sl);   // rho h sqrt(lam)/sqrt(pi), rho h = p
     const double E = erfc_nonneg(fabs(x), ex2);
     const bool into = sign > 0 ? x >= 0.0 : x < 0.0;
-    m.u[0] = into ? fma(-0.5, E, 1.0) : 0.5 * E;
+    const double hr = 0.5 * s.rho;
+    m.u[0] = into ? fma(-hr, E, s.rho) : hr * E;
     m.u[1] = fma(s.U, m.u[0], sign > 0 ? e : -e);
     recur_u<DIM>(s, m);
     fill_vx<DIM>(s, fc, m);
@@ -711,16 +705,16 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     psi_mom<DIM>(ml, pl0, pl1);
     psi_mom<DIM>(mr, pr0, pr1);
 #pragma unroll
-    for (int k = 0; k < NV; k++) Wc[k] = fma(sl.rho, pl0[k], sr.rho * pr0[k]);
+    for (int k = 0; k < NV; k++) Wc[k] = pl0[k] + pr0[k];
     Gm<DIM, 0, 0>(a1l, ml, t1);
     Gm<DIM, 0, 0>(a1r, mr, t2);
 #pragma unroll
-    for (int k = 0; k < NV; k++) Wcx[k] = fma(sl.rho, t1[k], sr.rho * t2[k]);
+    for (int k = 0; k < NV; k++) Wcx[k] = t1[k] + t2[k];
     if constexpr (DIM == 2) {
         Gm<DIM, 0, 0>(a2l, ml, t1);
         Gm<DIM, 0, 0>(a2r, mr, t2);
 #pragma unroll
-        for (int k = 0; k < NV; k++) Wcy[k] = fma(sl.rho, t1[k], sr.rho * t2[k]);
+        for (int k = 0; k < NV; k++) Wcy[k] = t1[k] + t2[k];
     }
     MState<DIM> sc;
     if (!make_state<DIM>(Wc, fc, sc)) return false;
@@ -824,8 +818,8 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
             Gm<DIM, 1, 0>(As, mh, L6);
 #pragma unroll
             for (int k = 0; k < NV; k++) {
-                acc0[k] = fma(st.rho, fma(A0[3], L4[k], fma(A0[4], L5[k], A0[5] * L6[k])), acc0[k]);
-                acc1[k] = fma(st.rho, fma(A1[3], L4[k], fma(A1[4], L5[k], A1[5] * L6[k])), acc1[k]);
+                acc0[k] = fma(A0[3], L4[k], fma(A0[4], L5[k], fma(A0[5], L6[k], acc0[k])));
+                acc1[k] = fma(A1[3], L4[k], fma(A1[4], L5[k], fma(A1[5], L6[k], acc1[k])));
             }
             if constexpr (PRFIX) {
                 // density moments of the side's three terms over its half line
@@ -838,9 +832,9 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
                 }
                 Gm<DIM, 0, 0>(As, mh, D6);
                 const double* D4 = side == 0 ? pl0 : pr0;
-                Qh[3] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D4), dotv<NV>(lv, L4)), Qh[3]);
-                Qh[4] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D5), dotv<NV>(lv, L5)), Qh[4]);
-                Qh[5] = fma(st.rho, fma(-sc.U, dotv<NV>(lv, D6), dotv<NV>(lv, L6)), Qh[5]);
+                Qh[3] += fma(-sc.U, dotv<NV>(lv, D4), dotv<NV>(lv, L4));
+                Qh[4] += fma(-sc.U, dotv<NV>(lv, D5), dotv<NV>(lv, L5));
+                Qh[5] += fma(-sc.U, dotv<NV>(lv, D6), dotv<NV>(lv, L6));
             }
         }
         if constexpr (PRFIX) {
