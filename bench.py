@@ -48,7 +48,7 @@ FLUX_FLOP_PER_GP_2D = (1665.6 + 1616.4) / 2
 FLUX_DRAM_BYTES_PER_GP = (113.03e6 + 113.80e6 + 106.85e6 + 107.77e6) / 4 / (2 * 512 * 513)
 # FP64 flop of one whole S2O4 step per cell-stage (all kernels, ncu DADD + DMUL + 2 x DFMA
 # over the 40 launches of one 512^2 four-quadrant step, troubled fraction 1.1 %).
-STEP_FLOP_PER_CELL_STAGE = 8569.7
+STEP_FLOP_PER_CELL_STAGE = 8477.8
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 
@@ -278,29 +278,36 @@ def bench_served(args, torch, hgks, P):
     print(json.dumps(line), flush=True)
 
 
-def bench_ns_tube(args, torch, hgks, P):
-    """2D Navier-Stokes viscous shock tube in [0,1] x [0,0.5] (Sec. 3.6 set-up) at Re = 1000,
-    Pr = 0.73 (energy-flux Prandtl fix), nx x nx/2 cells: K timed S2O4 steps on the device."""
-    nx = args.ns_nx
-    cfg, W, _ = P.viscous_shock_tube(nx, nx // 2, Re=1000.0, prandtl=0.73)
+def bench_single(args, torch, hgks, P):
+    """One solve of another configuration, K timed S2O4 steps on the device:
+    ns_tube: 2D Navier-Stokes viscous shock tube in [0,1] x [0,0.5] (Sec. 3.6 set-up) at
+             Re = 1000, Pr = 0.73 (energy-flux Prandtl fix), nx x nx/2 cells;
+    vortex:  isentropic vortex on the periodic [0,10]^2 (strength 5, tau = 0), nx^2 cells."""
+    nx = args.ns_nx if args.workload == "ns_tube" else args.vortex_n
+    if args.workload == "ns_tube":
+        cfg, W, _ = P.viscous_shock_tube(nx, nx // 2, Re=1000.0, prandtl=0.73)
+        label = "2D NS viscous shock tube, %dx%d, Re 1000, Pr 0.73, hybrid, S2O4" % (nx, nx // 2)
+    else:
+        cfg, W, _ = P.vortex_2d(nx)
+        label = "2D isentropic vortex, %d^2, periodic, tau = 0, hybrid, S2O4" % nx
     stream = torch.cuda.Stream()
     s = hgks.Solver(cfg, stream=stream)
     s.hgks_set_state(np.ascontiguousarray(W))
-    s.hgks_step(1.0, args.warmup, wait=True)
+    s.hgks_step(1e9, args.warmup, wait=True)
     s.hgks_set_timing(True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
-    s.hgks_step(1.0, args.steps, wait=False)
+    s.hgks_step(1e9, args.steps, wait=False)
     b.record(stream)
     stream.synchronize()
     ms = a.elapsed_time(b)
     tim = s.hgks_get_timing()
     st = s.hgks_get_stats()
     s.hgks_destroy_solver()
-    cells = nx * (nx // 2)
+    cells = int(np.prod(W.shape[1:]))
     tot = sum(v[0] for v in tim.values())
-    line = {"metric": METRIC, "workload": "2D NS viscous shock tube, %dx%d, Re 1000, Pr 0.73, hybrid, S2O4" % (nx, nx // 2),
+    line = {"metric": METRIC, "workload": label,
             "unit": UNIT, "value": cells * 2 * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
             "steps": args.steps, "status": int(st["status"]), "t": st["t"],
             "troubled_fraction": float(st["troubled"].sum()) / max(1, int(st["examined"].sum())),
@@ -383,8 +390,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ref-side", type=int, default=256, help="grid side of the oracle's bounded sample")
-    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube"])
+    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube", "vortex"])
     ap.add_argument("--ns-nx", type=int, default=1000, help="ns_tube: cells along x (ny = nx/2)")
+    ap.add_argument("--vortex-n", type=int, default=800, help="vortex: cells per side")
     ap.add_argument("--recon-cases", default="", help="comma-separated subset of the recon_cost cases")
     ap.add_argument("--solves", type=int, default=256)
     ap.add_argument("--requests", type=int, default=32)
@@ -423,8 +431,8 @@ def main():
         return bench_served(args, torch, hgks, P)
     if args.workload == "recon_cost":
         return bench_recon_cost(args, torch, hgks, P)
-    if args.workload == "ns_tube":
-        return bench_ns_tube(args, torch, hgks, P)
+    if args.workload in ("ns_tube", "vortex"):
+        return bench_single(args, torch, hgks, P)
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
