@@ -38,7 +38,7 @@ extern "C" {
 #define HGKS_EINVAL (-1)         /* invalid argument or configuration */
 #define HGKS_ENOMEM (-2)         /* device or host allocation failed */
 #define HGKS_ENONPHYSICAL (-3)   /* rho <= 0, p <= 0 or non-finite state detected on the device */
-#define HGKS_ETIMEOUT (-4)       /* a bounded device wait ran out */
+#define HGKS_ETIMEOUT (-4)       /* a bounded device wait ran out (reserved: no kernel of this library waits) */
 #define HGKS_ECUDA (-5)          /* a CUDA runtime call failed */
 
 /* boundary conditions (Sec. 3: periodic, non-reflecting, reflecting, symmetric, no-slip adiabatic;
@@ -179,6 +179,9 @@ typedef struct hgks_batch hgks_batch;
  * to stepping the solver alone.  The solvers keep their own state, dt, time and
  * counters; they must stay alive, and must not be stepped on their own, while
  * the batch exists.  stream: cudaStream_t cast to void* for all batched work.
+ * A solver's own stream is ordered with the batch stream by events: work
+ * enqueued on it before hgks_batch_step (hgks_set_state, ...) runs before the
+ * batched steps, work enqueued on it afterwards (hgks_get_state, ...) after them.
  * The batch's own device memory is O(n) (descriptors, block tables).
  * The paper describes one solve at a time; batching is this library's way of
  * filling one GPU with many small solves.  Errors: HGKS_EINVAL, HGKS_ENOMEM, HGKS_ECUDA. */

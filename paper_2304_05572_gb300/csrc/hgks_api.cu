@@ -476,6 +476,9 @@ struct hgks_batch {
     int tuned = 0;
     cudaEvent_t ev[2 * BK_COUNT];
     cudaEvent_t tend_ev = nullptr;   // marks the last copy out of h_tend
+    std::vector<cudaStream_t> others;   // the solvers' own streams other than the batch stream
+    std::vector<cudaEvent_t> other_ev;  // one per entry of others: work enqueued there before a step
+    cudaEvent_t done_ev = nullptr;      // the batch stream after the last enqueued step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long steps_enqueued = 0;
@@ -526,6 +529,16 @@ extern "C" int hgks_batch_create(hgks_solver* const* solvers, int n, void* strea
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tend, sizeof(double) * n);
     for (int k = 0; k < 2 * BK_COUNT && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tend_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        cudaStream_t st = solvers[i]->stream;
+        bool seen = st == b->stream;
+        for (cudaStream_t o : b->others) seen = seen || o == st;
+        if (seen) continue;
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) { b->others.push_back(st); b->other_ev.push_back(ev); }
+    }
     if (e != cudaSuccess) {
         set_err(g_create_err, "batch allocation failed: %s", cudaGetErrorString(e));
         hgks_batch_destroy(b);
@@ -550,6 +563,8 @@ extern "C" void hgks_batch_destroy(hgks_batch* b)
     if (b->graph) cudaGraphDestroy(b->graph);
     for (int k = 0; k < 2 * BK_COUNT; k++) if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->tend_ev) cudaEventDestroy(b->tend_ev);
+    if (b->done_ev) cudaEventDestroy(b->done_ev);
+    for (cudaEvent_t ev : b->other_ev) cudaEventDestroy(ev);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_boff) cudaFree(b->d_boff);
     if (b->d_tend) cudaFree(b->d_tend);
@@ -560,6 +575,11 @@ extern "C" void hgks_batch_destroy(hgks_batch* b)
 extern "C" int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, int flags)
 {
     if (!b || nsteps < 0) return HGKS_EINVAL;
+    // work already enqueued on the solvers' own streams (set_state, ...) runs first
+    for (size_t i = 0; i < b->others.size(); i++) {
+        CUDA_TRY(b, cudaEventRecord(b->other_ev[i], b->others[i]));
+        CUDA_TRY(b, cudaStreamWaitEvent(b->stream, b->other_ev[i], 0));
+    }
     if (t_end) {
         for (int i = 0; i < b->n; i++)
             if (!std::isfinite(t_end[i])) { set_err(b->err, "t_end[%d] is not finite", i); return HGKS_EINVAL; }
@@ -628,6 +648,11 @@ extern "C" int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, i
             CUDA_TRY(b, batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, nullptr));
         }
         b->steps_enqueued++;
+    }
+    // and work enqueued on them later (get_state, ...) runs after the batched steps
+    if (!b->others.empty()) {
+        CUDA_TRY(b, cudaEventRecord(b->done_ev, b->stream));
+        for (cudaStream_t o : b->others) CUDA_TRY(b, cudaStreamWaitEvent(o, b->done_ev, 0));
     }
     return HGKS_OK;
 }

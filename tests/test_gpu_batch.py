@@ -128,3 +128,25 @@ def test_failed_solver_stops_alone_and_others_continue():
     assert solvers[1].hgks_get_stats()["steps"] < 12
     assert solvers[0].hgks_get_stats()["steps"] == 12 and solvers[2].hgks_get_stats()["steps"] == 12
     b.hgks_batch_destroy()
+
+
+def test_solver_streams_are_ordered_with_the_batch_stream():
+    """Solvers on their own streams, the batch on a third: a state set on a solver's stream
+    just before hgks_batch_step is the one the batch advances, and hgks_get_state on the
+    solver's stream right after it (no hgks_batch_sync) sees the advanced state."""
+    import torch
+    cases = [P.riemann4_2d(n, seed=P.BATCH_SEED + 1 + k)[:2] for k, n in ((0, 40), (1, 56))]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    solvers = [hgks.Solver(cfg, stream=st) for (cfg, _), st in zip(cases, streams)]
+    zero = [np.zeros_like(W) + 1.0 for _, W in cases]
+    for s, z in zip(solvers, zero):
+        s.hgks_set_state(np.ascontiguousarray(z))
+    b = hgks.Batch(solvers, stream=torch.cuda.Stream())
+    for s, (cfg, W) in zip(solvers, cases):
+        s.hgks_set_state(np.ascontiguousarray(W))      # enqueued on the solver's own stream
+    b.hgks_batch_step([1e9, 1e9], nsteps=6, graph=True)
+    for s, (cfg, W) in zip(solvers, cases):
+        ref, t_ref, n_ref = _alone(cfg, W, 1e9, 6)
+        assert np.array_equal(s.hgks_get_state(), ref)
+        assert s.hgks_get_time() == t_ref
+    b.hgks_batch_destroy()
