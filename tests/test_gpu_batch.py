@@ -150,3 +150,26 @@ def test_solver_streams_are_ordered_with_the_batch_stream():
         assert np.array_equal(s.hgks_get_state(), ref)
         assert s.hgks_get_time() == t_ref
     b.hgks_batch_destroy()
+
+
+def test_batch_mixes_prandtl_fixed_and_bgk_solvers():
+    """Navier-Stokes solvers with Pr = 0.73 (the energy-flux fix) and Pr = 1 in one batch:
+    the batched flux launch serves both kinds of blocks, each bit-identical to its solo run."""
+    import torch
+    cases = [P.viscous_shock_tube(40, 20, Re=500.0, prandtl=0.73)[:2],
+             P.viscous_shock_tube(48, 24, Re=300.0)[:2],
+             P.viscous_shock_tube(32, 16, Re=800.0, prandtl=0.73)[:2]]
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cfg, W in cases:
+        s = hgks.Solver(cfg, stream=stream)
+        s.hgks_set_state(np.ascontiguousarray(W))
+        solvers.append(s)
+    b = hgks.Batch(solvers, stream=stream)
+    b.hgks_batch_step([1e9] * 3, nsteps=5, graph=True)
+    b.hgks_batch_sync()
+    for (cfg, W), s in zip(cases, solvers):
+        ref, t_ref, _ = _alone(cfg, W, 1e9, 5)
+        assert np.array_equal(s.hgks_get_state(), ref)
+        assert s.hgks_get_time() == t_ref
+    b.hgks_batch_destroy()
