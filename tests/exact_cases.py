@@ -33,3 +33,17 @@ def quartic_advection(dim, n, cfl):
     cfg = P.base_config(dim, n, n, 0.0, 1.0, 0.0, 1.0, fixed_dt=dt, tau_zero=1, bc=["extrap"] * 4,
                         recon_mode="linear")
     return cfg, np.ascontiguousarray(W), cons(dt), dt
+
+
+def all_troubled_1d(n=24, seed=5):
+    """A periodic 1D state whose density and pressure alternate between two levels from cell
+    to cell (with seeded noise): every cell is an extremum, so the indicator flags every cell
+    in both stages and the hybrid scheme is WENO-AO everywhere."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = np.arange(n)
+    rho = np.where(x % 2 == 0, 1.0, 3.0) * (1 + 0.2 * rng.random(n))
+    u = 0.1 * rng.standard_normal(n)
+    p = np.where(x % 2 == 0, 1.0, 2.5) * (1 + 0.2 * rng.random(n))
+    W = P.conservative(rho, u, 0 * u, p, dim=1)[:, None, :]
+    cfg = P.base_config(1, n, 1, 0.0, 1.0, bc=["periodic"] * 4)
+    return cfg, np.ascontiguousarray(W)

@@ -119,6 +119,19 @@ def test_sine_1d_final_time(mode):
     assert rel_diff(Wg, Wo) <= FINAL_TOL
 
 
+def test_shu_osher_steps_and_full_run():
+    """Shu-Osher shock / entropy-wave interaction (Sec. 3.2(b)), 400 cells: steps along the
+    run against the oracle, and the whole run to t = 1.8."""
+    cfg, W, t_end = P.shu_osher_1d(400)
+    W1, _, _, _ = check_step(cfg, W, "shu-osher step 0")
+    W2, t, _, _ = oracle.run(cfg, W, 1.0)
+    check_step(cfg, W2, "shu-osher t=1", t0=t)
+    Wg, tg, ng = hgks.run(cfg, W, t_end)
+    Wo, to, no, _ = oracle.run(cfg, W, t_end)
+    assert ng == no and tg == pytest.approx(to, abs=1e-14)
+    assert rel_diff(Wg, Wo) < 1e-8
+
+
 def test_blast_1d_positivity_path():
     cfg, W, t_end = P.blast_1d(200)
     W2, t, _, _ = oracle.run(cfg, W, 0.0262)      # just before the two blast waves collide
@@ -365,3 +378,15 @@ def test_checkpoint_resume_reproduces_the_same_bits():
     assert c.hgks_get_time() == t_ref
     assert np.array_equal(c.hgks_get_state(), ref)
     c.hgks_destroy_solver()
+
+
+def test_all_troubled_hybrid_is_wenoao_on_gpu():
+    """Every cell flagged (alternating two-level data): the GPU's hybrid step equals its
+    WENO-AO step bit for bit, and both match the oracle."""
+    from exact_cases import all_troubled_1d
+    cfg, W = all_troubled_1d()
+    Wo, _, fo, _ = check_step(cfg, W, "all troubled")
+    assert all(np.all(f == 1) for f in fo.values())
+    Wg_h, _, _ = gpu_step(cfg, W)
+    Wg_a, _, _ = gpu_step(dict(cfg, recon_mode="wenoao"), W)
+    assert np.array_equal(Wg_h, Wg_a)

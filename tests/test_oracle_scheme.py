@@ -399,3 +399,16 @@ def test_s2o4_advects_a_quartic_exactly(dim):
         assert np.abs(Wo[k][inner] - exact[k][inner]).max() <= 2e-15 * max(scale, 1.0) * 10
     fourth = (0.7 + 0.4) ** 4 * dt ** 4 * 30.0 / (4 * 3 * 2) * 24
     assert fourth > 1e-9
+
+
+def test_hybrid_equals_wenoao_when_every_cell_is_troubled():
+    """The converse of hybrid = linear on smooth data: when the indicator flags every cell
+    (alternating two-level data), the hybrid step is the WENO-AO step, bit for bit."""
+    from exact_cases import all_troubled_1d
+    cfg, W = all_troubled_1d()
+    Wh, dt, fl = oracle.step_flags(cfg, W)
+    assert all(np.all(f == 1) for f in fl.values())
+    Wa, dta, _ = oracle.step_flags(dict(cfg, recon_mode="wenoao"), W)
+    Wl, _, _ = oracle.step_flags(dict(cfg, recon_mode="linear"), W)
+    assert dt == dta and np.array_equal(Wh, Wa)
+    assert not np.array_equal(Wh, Wl)
