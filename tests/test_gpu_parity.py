@@ -419,3 +419,23 @@ def test_gpu_reproduces_the_printed_2d_accuracy_table():
         Wg, t, _ = hgks.run(cfg, W, t_end)
         err = _norms(Wg[0] - P.sine_2d_exact(n, t))
         assert np.all(np.abs(err / ref[inv_h] - 1.0) < 0.05), (inv_h, err, ref[inv_h])
+
+
+def test_full_size_diagonal_symmetry_and_conservation():
+    """Properties that hold at any size, checked on the 1024^2 grid the benchmark runs:
+    quadrant data symmetric under x <-> y with u <-> v stays symmetric (to round-off) over
+    10 steps, and on a periodic domain the totals of every conserved variable stay fixed."""
+    st = [(1.0, 0.2, 0.2, 1.0), (0.5, 0.1, -0.3, 0.6), (0.8, -0.4, -0.4, 0.9), (0.5, -0.3, 0.1, 0.6)]
+    n = 1024
+    cfg = P.base_config(2, n, n, 0, 1, 0, 1, c1=0.01, c2=1.0, bc=["extrap"] * 4)
+    W = P._quadrants(n, n, st)
+    Wg, _, steps = hgks.run(cfg, W, 1.0, max_steps=10)
+    assert steps == 10
+    scale = np.abs(Wg).reshape(4, -1).max(axis=1)
+    assert np.abs(Wg[0] - Wg[0].T).max() <= 1e-12 * scale[0]
+    assert np.abs(Wg[1] - Wg[2].T).max() <= 1e-12 * max(scale[1], scale[2])
+    assert np.abs(Wg[3] - Wg[3].T).max() <= 1e-12 * scale[3]
+    cfg_p, Wp, _ = P.random_smooth_2d(n, n, seed=11, amp=0.2)
+    Wq, _, _ = hgks.run(cfg_p, Wp, 1.0, max_steps=5)
+    tot0, tot1 = Wp.reshape(4, -1).sum(axis=1), Wq.reshape(4, -1).sum(axis=1)
+    assert np.all(np.abs(tot1 - tot0) <= 1e-12 * np.abs(Wp).reshape(4, -1).sum(axis=1))
