@@ -13,6 +13,12 @@ With --gpus N > 1 (launched under torchrun) every rank advances its own
 independent replica (the solves do not exchange data) and the value is the
 aggregate over ranks divided by the maximum time over ranks.
 
+The default line also carries "served": a small seeded burst of mixed 1D/2D solves
+through the continuous-batching server against the same requests one at a time
+(throughput, p50/p99 latency, bitwise equality of the results); --no-served skips it.
+Other workloads (--workload batched | served | recon_cost | ns_tube | vortex) print
+their own line.
+
 --impl reference times the CPU oracle (the plain FP64 restatement of the
 paper's method) on the host cores, on a bounded sample of the same workload.
 """
@@ -236,14 +242,14 @@ def bench_batched(args, torch, hgks, P):
     print(json.dumps(line), flush=True)
 
 
-def bench_served(args, torch, hgks, P):
+def run_served(torch, P, requests, rate, max_1d, max_2d, max_ns, budget_gb, steps_per_iter):
     """Seeded Poisson stream of mixed solves through the continuous-batching server, and
-    the same trace served one solve at a time (FIFO, each solve alone on the GPU)."""
+    the same trace served one solve at a time (FIFO, each solve alone on the GPU).
+    Returns the figures as a dict."""
     from paper_2304_05572_gb300 import server
-    trace = P.served_trace(n_requests=args.requests, rate=args.rate, max_1d=args.max_1d, max_2d=args.max_2d,
-                           max_ns=args.max_ns)
+    trace = P.served_trace(n_requests=requests, rate=rate, max_1d=max_1d, max_2d=max_2d, max_ns=max_ns)
     stream = torch.cuda.Stream()
-    srv = server.Server(budget_bytes=args.budget_gb * 1e9, stream=stream, steps_per_iter=args.steps_per_iter,
+    srv = server.Server(budget_bytes=budget_gb * 1e9, stream=stream, steps_per_iter=steps_per_iter,
                         autotune=False)
     res = srv.run(trace)
     served_wall = srv.wall
@@ -264,17 +270,22 @@ def bench_served(args, torch, hgks, P):
         same = same and np.array_equal(out, res[r["id"]]["W"])
     plain_wall = time.perf_counter() - t0
     plain_lat = np.array([done_at[r["id"]] for r in trace])
-    line = {"metric": METRIC, "workload": "served: %d requests, Poisson rate %.1f/s (PCG64 seed %d), mix of 1D shock "
+    return {"workload": "served: %d requests, Poisson rate %.1f/s (PCG64 seed %d), mix of 1D shock "
             "tubes <= %d cells, 2D Riemann/vortex <= %d^2, 2D NS shock tubes <= %dx%d, t_end ~ U[0.05, 0.3], "
-            "budget %.0f GB" % (len(trace), args.rate, P.SERVE_SEED, args.max_1d, args.max_2d, args.max_ns,
-                                args.max_ns // 2, args.budget_gb),
+            "budget %.0f GB" % (len(trace), rate, P.SERVE_SEED, max_1d, max_2d, max_ns, max_ns // 2, budget_gb),
             "unit": UNIT, "value": work / served_wall / 1e6, "plain_value": work / plain_wall / 1e6,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "plain_p50_latency_s": float(np.percentile(plain_lat, 50)),
             "plain_p99_latency_s": float(np.percentile(plain_lat, 99)),
             "served_wall_s": served_wall, "plain_wall_s": plain_wall, "iterations": srv.iterations,
-            "peak_resident_solves": srv.peak_resident, "results_bitwise_equal_alone": bool(same),
-            "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+            "peak_resident_solves": srv.peak_resident, "results_bitwise_equal_alone": bool(same)}
+
+
+def bench_served(args, torch, hgks, P):
+    """The served workload at the sizes given on the command line, as its own JSON line."""
+    d = run_served(torch, P, args.requests, args.rate, args.max_1d, args.max_2d, args.max_ns, args.budget_gb,
+                   args.steps_per_iter)
+    line = {"metric": METRIC, **d, "dtype": "f64", "data": "synthetic", "higher_is_better": True}
     print(json.dumps(line), flush=True)
 
 
@@ -388,6 +399,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true", help="skip the small served-vs-plain run of the default line")
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ref-side", type=int, default=256, help="grid side of the oracle's bounded sample")
     ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube", "vortex"])
@@ -538,6 +550,13 @@ def main():
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
+    if rank == 0 and world == 1 and not args.no_served:
+        # the metric's served-vs-plain part: a small burst of mixed solves through the server
+        # and the same requests one at a time (both bitwise equal), with p50 / p99 latency
+        try:
+            line["served"] = run_served(torch, P, 16, 200.0, 2048, 256, 256, 150.0, 8)
+        except Exception as e:  # pragma: no cover
+            line["served"] = {"failed": str(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             v, secs, cores = cpu_oracle_rate(N_SIDE, 1)
