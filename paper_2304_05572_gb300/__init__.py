@@ -2,8 +2,9 @@
 hybrid WENO-AO reconstruction (arXiv 2304.05572).
 
 The computation runs in the CUDA library behind the C ABI of ``include/hgks.h``;
-``hgks`` is its Python binding (ctypes, argument marshalling only) and
-``problems`` holds the seeded initial data of the test problems.
+``hgks`` is its Python binding (ctypes, argument marshalling only),
+``problems`` holds the seeded initial data of the test problems and of the
+benchmark workloads, and ``server`` is the continuous-batching solve server.
 """
 from . import problems  # noqa: F401
 
