@@ -547,6 +547,10 @@ def main():
         "gpu_launches": launches,
         "roofline": roofline,
         "kernel_time_share": shares,
+        # the same throughput with the dt reduction and the ghost fills taken out (the value above
+        # is the whole step, those included)
+        "value_without_dt_and_ghost": value / max(1e-9, 1.0 - shares.get("dt", 0.0) - shares.get("ghost", 0.0)
+                                                  - shares.get("misc", 0.0)),
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
