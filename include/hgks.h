@@ -22,7 +22,8 @@
  *     creation (NULL = the legacy default stream).  A solver is not thread-safe;
  *     distinct solvers on distinct streams may be used from distinct threads.
  *   - hgks_last_error(s) returns a static, human-readable description of the
- *     last failure on s (or of the last create failure when s is NULL).
+ *     last failure on s (or, when s is NULL, of the calling thread's last failed
+ *     hgks_create_solver / hgks_batch_create / hgks_step_noalloc call).
  */
 #ifndef HGKS_H
 #define HGKS_H
@@ -223,6 +224,19 @@ const char* hgks_batch_last_error(const hgks_batch* b);
 void hgks_batch_destroy(hgks_batch* b);
 
 /* ------------------------------------------------------------------------ */
+/* FP64 rate probe (measurement helper; the paper has no counterpart).       */
+/* ------------------------------------------------------------------------ */
+
+/* Measure the FP64 fused-multiply-add rate of the current device: 8 blocks of
+ * 256 threads per SM each run 8 independent DFMA chains (4 launches, CUDA
+ * events on `stream`, NULL = default stream; the call waits for them).
+ * *tflops = 2 x DFMA per second / 1e12 (the FP64 peak every kernel of the
+ * step is measured against), *ms (may be NULL) the time of the 4 launches,
+ * *sms (may be NULL) the device's SM count.  Errors: HGKS_EINVAL (tflops NULL),
+ * HGKS_ECUDA (message in hgks_last_error(NULL)). */
+int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free single step.                                              */
 /* ------------------------------------------------------------------------ */
 
@@ -236,13 +250,22 @@ void hgks_batch_destroy(hgks_batch* b);
  * device-wide synchronisation cudaMalloc/cudaFree may cause.  The paper has no
  * counterpart; the arithmetic is exactly that of hgks_step on a solver created
  * from *cfg (same kernels, dt from the CFL rule or cfg->fixed_dt, no t_end
- * clipping).  The step starts at t = 0: boundaries that move with time
- * (HGKS_BC_SHOCK_TRACK) take their t = 0 position.
+ * clipping), so the result is bit-identical to that step.  The step starts at
+ * t = 0: boundaries that move with time (HGKS_BC_SHOCK_TRACK) take their t = 0
+ * position.
  *
  * W_in, W_out: device memory of the current device, [nv][ny][nx] FP64 as
  * everywhere in this ABI, owned by the caller; they may be the same buffer.
+ * status: NULL, or one int the device can be copied to (device memory, or
+ * host memory); when the stream reaches the end of the step it holds 0, or
+ * HGKS_ENONPHYSICAL if the step met a non-physical state (rho <= 0, p <= 0 or
+ * non-finite; W_out is then not a valid state).  The copy is a cudaMemcpyAsync
+ * with cudaMemcpyDefault on the stream: with device or pinned host memory the
+ * call does not wait, with pageable host memory it waits for the step.
+ * Without a status word a non-physical step goes unreported.
  * stream: cudaStream_t cast to void* (NULL = default stream).  The call
- * enqueues the work and returns; W_out is ready when the stream reaches it.
+ * enqueues the work and returns; W_out (and *status) are ready when the stream
+ * reaches them.
  *
  * Every intermediate buffer lives in one file-scope device array of
  * HGKS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
@@ -255,9 +278,9 @@ void hgks_batch_destroy(hgks_batch* b);
  * the one array: calls whose work overlaps on the GPU race and corrupt each
  * other, so issue them one after another (for example on one stream).  Each
  * call clears the array before use.
- * Errors: HGKS_EINVAL (bad config, NULL buffer, grid too large; message in
- * hgks_last_error(NULL)), HGKS_ECUDA. */
-int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, void* stream);
+ * Errors: HGKS_EINVAL (bad config, NULL buffer, grid too large), HGKS_ECUDA;
+ * the message is in hgks_last_error(NULL), kept per calling thread. */
+int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, int* status, void* stream);
 
 #ifdef __cplusplus
 }

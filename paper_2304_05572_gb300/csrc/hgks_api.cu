@@ -700,6 +700,37 @@ extern "C" int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long
 extern "C" const char* hgks_batch_last_error(const hgks_batch* b) { return b ? b->err : g_create_err; }
 
 // ---------------------------------------------------------------------------
+// FP64 rate of the current device (the denominator of the benchmark's roofline).
+extern "C" int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms)
+{
+    if (!tflops) return HGKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nsm = device_sm_count();
+    const int blocks = nsm * 8, iters = 4096;      // 8 blocks of 256 threads per SM: 64 warps
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch_dfma_probe(st, blocks, 64);     // loads the kernel
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int r = 0; r < 4 && e == cudaSuccess; r++) e = launch_dfma_probe(st, blocks, iters);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "hgks_probe_fp64: %s", cudaGetErrorString(e));
+        return HGKS_ECUDA;
+    }
+    const double flop = 4.0 * blocks * 256.0 * iters * 8.0 * 2.0;
+    *tflops = flop / (t * 1e-3) / 1e12;
+    if (ms) *ms = t;
+    if (sms) *sms = nsm;
+    return HGKS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free single step (hgks_step_noalloc): the same S2O4 step as a solver
 // performs, with every intermediate buffer carved out of one file-scope device
 // array instead of a cudaMalloc'd pool.  The array is part of the library image,
@@ -717,7 +748,7 @@ std::mutex g_noalloc_mutex;
 
 }  // namespace
 
-extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, void* stream)
+extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, double* W_out, int* status, void* stream)
 {
     int st = validate(cfg, g_create_err);
     if (st != HGKS_OK) return st;
@@ -801,6 +832,10 @@ extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, dou
         e = cudaMemcpy2DAsync(W_out + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),
                               s.W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
                               (size_t)g.nx * sizeof(double), (size_t)g.ny, cudaMemcpyDeviceToDevice, s.stream);
+    // the status the step latched on the device (0 or HGKS_ENONPHYSICAL), for the caller to read
+    // once the stream has passed this point; no host wait here
+    if (status && e == cudaSuccess)
+        e = cudaMemcpyAsync(status, &s.ctrl->status, sizeof(int), cudaMemcpyDefault, s.stream);
     if (e != cudaSuccess) {
         set_err(g_create_err, "hgks_step_noalloc: %s", cudaGetErrorString(e));
         return HGKS_ECUDA;

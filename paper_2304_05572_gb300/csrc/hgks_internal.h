@@ -135,6 +135,8 @@ extern const char* kclass_names[KC_COUNT];
 cudaError_t launch_step(hgks_solver* s, double t_end);
 cudaError_t launch_set_time(hgks_solver* s, double t0);
 int device_sm_count();
+// FP64 rate probe: `blocks` blocks of 256 threads, 8 DFMA chains of `iters` steps per thread
+cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters);
 
 // batched execution (hgks_kernels.cu)
 void batch_fill_desc(const hgks_solver* s, SolveDesc& d);

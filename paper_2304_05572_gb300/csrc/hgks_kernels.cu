@@ -797,7 +797,32 @@ __global__ void kb_update(const SolveDesc* __restrict__ D, const int* __restrict
 
 inline unsigned int blocks_for(long long n, int tpb) { return (unsigned int)((n + tpb - 1) / tpb); }
 
+// ---------------------------------------------------------------- FP64 rate probe
+// Eight independent DFMA chains per thread: with 8 warps per SM scheduler slot the FP64 pipe
+// never waits on a result, so the launch runs at the FMA issue rate of the device.  The sum is
+// stored only under a condition the data never meet, which keeps the chains live.
+__device__ double g_probe_sink;
+
+__global__ void __launch_bounds__(256) k_dfma_probe(int iters, double seed)
+{
+    const double m = 0.9999999999, c = 1e-12;
+    double a0 = seed + threadIdx.x * 1e-9, a1 = a0 + 1e-3, a2 = a0 + 2e-3, a3 = a0 + 3e-3;
+    double a4 = a0 + 4e-3, a5 = a0 + 5e-3, a6 = a0 + 6e-3, a7 = a0 + 7e-3;
+    for (int i = 0; i < iters; i++) {
+        a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+        a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+    }
+    const double s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s == -1.0) g_probe_sink = s;
+}
+
 }  // namespace
+
+cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters)
+{
+    k_dfma_probe<<<blocks, 256, 0, st>>>(iters, 1.0);
+    return cudaGetLastError();
+}
 
 int device_sm_count()
 {

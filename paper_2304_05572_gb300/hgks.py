@@ -35,7 +35,7 @@ EXPORTED = [
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
     "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status", "hgks_batch_info",
     "hgks_batch_last_error",
-    "hgks_batch_destroy", "hgks_step_noalloc",
+    "hgks_batch_destroy", "hgks_probe_fp64", "hgks_step_noalloc",
 ]
 HGKS_BATCH_GRAPH = 1
 HGKS_BATCH_AUTOTUNE = 2
@@ -113,7 +113,8 @@ def lib():
         L.hgks_batch_last_error.restype = ctypes.c_char_p
         L.hgks_batch_destroy.argtypes = [vp]
         L.hgks_batch_destroy.restype = None
-        L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp]
+        L.hgks_probe_fp64.argtypes = [vp, dp, dp, ip]
+        L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp, vp]
         _lib = L
         return L
 
@@ -339,15 +340,48 @@ def run(cfg: dict, W, t_end: float, max_steps: int = 1 << 30, t0: float = 0.0):
         s.hgks_destroy_solver()
 
 
-def hgks_step_noalloc(cfg: dict, W_in, W_out, stream=None):
-    """One S2O4 step W_in -> W_out (CUDA float64 tensors [nv][ny][nx]) without any device
-    allocation: the intermediates live in the library's static scratch (see include/hgks.h)."""
+def hgks_probe_fp64(stream=None):
+    """FP64 FMA rate of the current device: (TFLOP/s, ms of the probe, SM count)."""
+    tf, ms, sms = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rc = lib().hgks_probe_fp64(ctypes.c_void_p(st or 0), ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms))
+    if rc != HGKS_OK:
+        raise HGKSError(rc, lib().hgks_last_error(None).decode())
+    return tf.value, ms.value, sms.value
+
+
+def hgks_step_noalloc(cfg: dict, W_in, W_out, stream=None, status=None):
+    """One S2O4 step W_in -> W_out (CUDA float64 tensors [nv][ny][nx] on the current device)
+    without any device allocation: the intermediates live in the library's static scratch
+    (see include/hgks.h).  status: None, or a one-element int32 tensor (device or host) /
+    numpy array that receives 0 or HGKS_ENONPHYSICAL when the stream reaches the end of
+    the step."""
     c = make_config(cfg)
     pin, din = _ptr(W_in)
     pout, dout = _ptr(W_out)
     if not (din and dout):
         raise ValueError("hgks_step_noalloc takes device tensors")
+    import torch
+    dev = torch.cuda.current_device()
+    if W_in.device.index != dev or W_out.device.index != dev:
+        raise ValueError("W_in and W_out must live on the current CUDA device (%d)" % dev)
+    n = (c.dim + 2) * c.nx * c.ny
+    if W_in.numel() != n or W_out.numel() != n:
+        raise ValueError("W_in and W_out must hold (dim+2)*nx*ny = %d values (got %d and %d)"
+                         % (n, W_in.numel(), W_out.numel()))
+    ps = None
+    if status is not None:
+        if isinstance(status, np.ndarray):
+            if status.dtype != np.int32 or status.size != 1 or not status.flags["C_CONTIGUOUS"]:
+                raise ValueError("status must be one contiguous int32")
+            ps = ctypes.c_void_p(status.ctypes.data)
+        else:
+            if str(status.dtype) != "torch.int32" or status.numel() != 1 or not status.is_contiguous():
+                raise ValueError("status must be one contiguous int32")
+            if status.is_cuda and status.device.index != dev:
+                raise ValueError("status must live on the current CUDA device (%d)" % dev)
+            ps = ctypes.c_void_p(status.data_ptr())
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-    rc = lib().hgks_step_noalloc(ctypes.byref(c), pin, pout, ctypes.c_void_p(st or 0))
+    rc = lib().hgks_step_noalloc(ctypes.byref(c), pin, pout, ps, ctypes.c_void_p(st or 0))
     if rc != HGKS_OK:
         raise HGKSError(rc, lib().hgks_last_error(None).decode())

@@ -21,7 +21,7 @@ def L():
 def _declared():
     src = open(os.path.join(ROOT, "include", "hgks.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hgks_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hgks_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(L):
