@@ -31,7 +31,7 @@ _lib = None
 BC = {"periodic": 0, "extrap": 1, "reflect": 2, "symmetry": 3, "noslip": 4, "inflow": 5, "shock_wall": 6,
       "shock_track": 7}
 RECON = {"hybrid": 0, "linear": 1, "wenoao": 2}
-ZETA1 = {"A": 0, "B": 1, "C": 2}
+ZETA1 = {"A": 0, "B": 1, "C": 2, "D": 3}
 NG = 4
 
 

@@ -42,7 +42,7 @@
 enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4,
        BC_INFLOW = 5, BC_SHOCK_WALL = 6, BC_SHOCK_TRACK = 7 };
 enum { RECON_HYBRID = 0, RECON_LINEAR = 1, RECON_WENOAO = 2 };
-enum { ZETA1_A = 0, ZETA1_B = 1, ZETA1_C = 2 };
+enum { ZETA1_A = 0, ZETA1_B = 1, ZETA1_C = 2, ZETA1_D = 3 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ENONPHYSICAL = -3 };
 
 typedef struct {
@@ -438,8 +438,12 @@ static int gks_point_flux(const or_config* cfg, const double* Wl, const double* 
  * Z1 = 17 zeta1 dx^2 precomputed.  Step 3 uses the conservative quadratic on
  * I_{i-1}, I_i, I_{i+1}: ahat1 = (Q_{i+1}-Q_{i-1})/2, ahat2 = ((Q_{i-1}+Q_{i+1}) - 2Q_i)/2.
  * Reading: both intervals are closed (|xbar| <= 5/2 is "inside", |xbar-xhat| <= 1/4
- * is non-troubled); the 1e-30 guard of Step 3 is applied in cell units. */
-static int indicator_raw(const double* q, double Z1)
+ * is non-troubled); the 1e-30 guard of Step 3 is applied in cell units.
+ * hmix > 0 selects reading D of Step 3 (zeta1 reading D): the printed abar1, abar2
+ * carry dx, so xbar is a length (xbar dx), while the conservative quadratic of Step 3,
+ * whose coefficients are not printed, is taken in cell units, so xhat stays a cell
+ * count; the test is then |xbar hmix - xhat| <= hmix/4 with hmix = dx (zeta2 = dx/4). */
+static int indicator_raw(const double* q, double Z1, double hmix)
 {
     double D = fma(-10.0, q[2], fma(4.0, q[0], q[1]) + fma(4.0, q[4], q[3]));
     if (fabs(D) <= Z1) return 0;                                    /* Step 1 */
@@ -452,7 +456,11 @@ static int indicator_raw(const double* q, double Z1)
     double ah2 = 0.5 * ((q[1] + q[3]) - 2.0 * q[2]);
     double den = 2.0 * ah2 + (ah2 == 0.0 ? 1e-30 : 0.0);
     double xhat = -ah1 / den;
-    if (fabs(xbar - xhat) <= 0.25) return 0;                        /* Step 3 */
+    if (hmix > 0.0) {
+        if (fabs(xbar * hmix - xhat) <= 0.25 * hmix) return 0;     /* Step 3, reading D */
+    } else if (fabs(xbar - xhat) <= 0.25) {
+        return 0;                                                   /* Step 3 */
+    }
     return 1;
 }
 
@@ -767,14 +775,16 @@ typedef struct {
     int nv, NX, NY;          /* padded extents */
     double dx, dy, K;
     double Z1x, Z1y;         /* Step-1 thresholds in cell units, per direction */
+    double hmx, hmy;         /* reading D of Step 3: the cell size per direction, else 0 */
     ao_consts ao;
 } grid;
 
 static double zeta1_scaled(int mode, double h)
 {
     /* Z1 = 17 zeta1 h^2.  Reading B (default): zeta1 = 5/(17 h).
-       A: zeta1 = (5/17) h.  C: zeta1 = 5/17 in cell units. */
-    if (mode == ZETA1_A) return 5.0 * h * h * h;
+       A: zeta1 = (5/17) h.  C: zeta1 = 5/17 in cell units.  D: zeta1 as A, and Step 3
+       compares a length with a cell count (see indicator_raw). */
+    if (mode == ZETA1_A || mode == ZETA1_D) return 5.0 * h * h * h;
     if (mode == ZETA1_C) return 5.0;
     return 5.0 * h;
 }
@@ -792,6 +802,8 @@ static int grid_setup(const or_config* c, grid* g)
     g->K = dof_K(c->dim, c->gamma);
     g->Z1x = zeta1_scaled(c->zeta1_mode, g->dx);
     g->Z1y = zeta1_scaled(c->zeta1_mode, g->dy);
+    g->hmx = c->zeta1_mode == ZETA1_D ? g->dx : 0.0;
+    g->hmy = c->zeta1_mode == ZETA1_D ? g->dy : 0.0;
     ao_setup(c->gamma_hi, c->gamma_lo, c->eps, &g->ao);
     return OR_OK;
 }
@@ -895,6 +907,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
     int nt = dim == 2 ? (dir == 0 ? c->ny : c->nx) : 1;
     double hn = dir == 0 ? g->dx : g->dy, ht = dir == 0 ? g->dy : g->dx;
     double Z1n = dir == 0 ? g->Z1x : g->Z1y, Z1t = dir == 0 ? g->Z1y : g->Z1x;
+    double Hn = dir == 0 ? g->hmx : g->hmy, Ht = dir == 0 ? g->hmy : g->hmx;
     double inv12hn = 1.0 / (12.0 * hn);
     int th = dim == 2 ? 3 : 0;                 /* ghost lines needed tangentially */
     int tlo = -th, thi = nt + th;              /* lines [tlo, thi) */
@@ -929,7 +942,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
                 for (int k = 0; k < nv; k++) {
                     double q[5];
                     for (int s = 0; s < 5; s++) q[s] = QL(k, t, n - 2 + s);
-                    tr |= indicator_raw(q, Z1n);
+                    tr |= indicator_raw(q, Z1n, Hn);
                     if (fo && fo->nmargin) mg = fmin(mg, indicator_margin(q, Z1n));
                 }
             rawp[n + 2] = (uint8_t)tr;
@@ -1008,7 +1021,7 @@ static int sweep(const grid* g, const double* Wp, int dir, double dt, double* Fd
                                     int tt = t + dt3 - 2 + s;
                                     q[s] = line[((size_t)(tt - tlo) * nm + m) * 4 * nv + X * nv + k];
                                 }
-                                tr |= indicator_raw(q, Z1t);
+                                tr |= indicator_raw(q, Z1t, Ht);
                                 if (fo && fo->tmargin) tmg = fmin(tmg, indicator_margin(q, Z1t));
                             }
                         raw3[dt3 + 1] = tr;
@@ -1393,7 +1406,7 @@ int or_point_flux(const or_config* cfg, const double* Wl, const double* Wlx, con
     return gks_point_flux(cfg, Wl, Wlx, Wly, Wr, Wrx, Wry, dt, Fdt, Fhalf);
 }
 
-int or_indicator(const double* q5, double Z1) { return indicator_raw(q5, Z1); }
+int or_indicator(const double* q5, double Z1) { return indicator_raw(q5, Z1, 0.0); }
 double or_zeta1_scaled(int mode, double h) { return zeta1_scaled(mode, h); }
 
 void or_linear_face(const double* q5, double inv12h, int side, double* val, double* der)
