@@ -580,6 +580,50 @@ HGKS_HD __forceinline__ void Gm(const double* a, const Mom<DIM>& m, double* out)
     }
 }
 
+// The two slope moments of one side that share a slope, 2D, in one pass over the shared sums:
+//   Gm_x: G(0,0) and G(2,0) of the normal slope a1 (the x-slope of the equilibrium, Eq. (47), and
+//         the u^2 part of the (a1 u + a2 v) g flux moment of Eq. (10));
+//   Gm_y: G(0,0) and G(1,1) of the tangential slope a2 (the y-slope of the equilibrium and the
+//         u v part of the same flux moment).
+// Au(n) = a0 u_n + a1 u_{n+1} + a3/2 u_{n+2} and Bv(m) = a2 v_{m+1} + a3/2 (v_{m+2} + x2 v_m) are
+// formed once for both moments (and T(2,0) once for both in Gm_x).
+HGKS_HD __forceinline__ void Gm_x(const double* a, const Mom<2>& m, double* g00, double* g20)
+{
+    const double ha3 = 0.5 * a[3];
+    double Au[5], Bv[3];
+#pragma unroll
+    for (int n = 0; n < 5; n++) Au[n] = fma(a[1], m.u[n + 1], fma(ha3, m.u[n + 2], a[0] * m.u[n]));
+#pragma unroll
+    for (int k = 0; k < 3; k++) Bv[k] = fma(a[2], m.v[k + 1], ha3 * fma(m.x2, m.v[k], m.v[k + 2]));
+    auto T = [&](int n, int k) { return fma(m.v[k], Au[n], m.u[n] * Bv[k]); };
+    const double bx = fma(a[2], m.v[1], ha3 * m.v[2]);
+    auto Tx = [&](int n) { return fma(m.x2, fma(m.v[0], Au[n], m.u[n] * bx), ha3 * m.x4 * (m.u[n] * m.v[0])); };
+    const double T20 = T(2, 0);
+    g00[0] = T(0, 0); g00[1] = T(1, 0); g00[2] = T(0, 1);
+    g00[3] = 0.5 * (T20 + T(0, 2) + Tx(0));
+    g20[0] = T20; g20[1] = T(3, 0); g20[2] = T(2, 1);
+    g20[3] = 0.5 * (T(4, 0) + T(2, 2) + Tx(2));
+}
+
+HGKS_HD __forceinline__ void Gm_y(const double* a, const Mom<2>& m, double* g00, double* g11)
+{
+    const double ha3 = 0.5 * a[3];
+    double Au[4], Bv[4];
+#pragma unroll
+    for (int n = 0; n < 4; n++) Au[n] = fma(a[1], m.u[n + 1], fma(ha3, m.u[n + 2], a[0] * m.u[n]));
+#pragma unroll
+    for (int k = 0; k < 4; k++) Bv[k] = fma(a[2], m.v[k + 1], ha3 * fma(m.x2, m.v[k], m.v[k + 2]));
+    auto T = [&](int n, int k) { return fma(m.v[k], Au[n], m.u[n] * Bv[k]); };
+    auto Tx = [&](int n, int k) {
+        return fma(m.x2, fma(m.v[k], Au[n], m.u[n] * fma(a[2], m.v[k + 1], ha3 * m.v[k + 2])),
+                   ha3 * m.x4 * (m.u[n] * m.v[k]));
+    };
+    g00[0] = T(0, 0); g00[1] = T(1, 0); g00[2] = T(0, 1);
+    g00[3] = 0.5 * (T(2, 0) + T(0, 2) + Tx(0, 0));
+    g11[0] = T(1, 1); g11[1] = T(2, 1); g11[2] = T(1, 2);
+    g11[3] = 0.5 * (T(3, 1) + T(1, 3) + Tx(1, 1));
+}
+
 template <int DIM>
 HGKS_HD __forceinline__ void fill_vx(const MState<DIM>& s, const FluxConst& fc, Mom<DIM>& m)
 {
@@ -706,15 +750,38 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     psi_mom<DIM>(mr, pr0, pr1);
 #pragma unroll
     for (int k = 0; k < NV; k++) Wc[k] = pl0[k] + pr0[k];
-    Gm<DIM, 0, 0>(a1l, ml, t1);
-    Gm<DIM, 0, 0>(a1r, mr, t2);
+    // (2D: the u^2 and u v flux moments of the side slopes, L5 of Eq. (10), come out of the same
+    // passes and are kept for the non-equilibrium terms below)
+    double L5l[NV], L5r[NV];
+    if (DIM == 2 && fc.tau_zero) {
+        // tau = 0: no non-equilibrium terms, only the equilibrium slopes
+        Gm<DIM, 0, 0>(a1l, ml, t1);
+        Gm<DIM, 0, 0>(a1r, mr, t2);
 #pragma unroll
-    for (int k = 0; k < NV; k++) Wcx[k] = t1[k] + t2[k];
-    if constexpr (DIM == 2) {
+        for (int k = 0; k < NV; k++) Wcx[k] = t1[k] + t2[k];
         Gm<DIM, 0, 0>(a2l, ml, t1);
         Gm<DIM, 0, 0>(a2r, mr, t2);
 #pragma unroll
         for (int k = 0; k < NV; k++) Wcy[k] = t1[k] + t2[k];
+    } else if constexpr (DIM == 2) {
+        double u1[NV], u2[NV];
+        Gm_x(a1l, ml, t1, L5l);
+        Gm_x(a1r, mr, t2, L5r);
+#pragma unroll
+        for (int k = 0; k < NV; k++) Wcx[k] = t1[k] + t2[k];
+        Gm_y(a2l, ml, t1, u1);
+        Gm_y(a2r, mr, t2, u2);
+#pragma unroll
+        for (int k = 0; k < NV; k++) { Wcy[k] = t1[k] + t2[k]; L5l[k] += u1[k]; L5r[k] += u2[k]; }
+    } else {
+        Gm<DIM, 0, 0>(a1l, ml, t1);
+        Gm<DIM, 0, 0>(a1r, mr, t2);
+#pragma unroll
+        for (int k = 0; k < NV; k++) Wcx[k] = t1[k] + t2[k];
+        if (!fc.tau_zero) {
+            Gm<DIM, 2, 0>(a1l, ml, L5l);
+            Gm<DIM, 2, 0>(a1r, mr, L5r);
+        }
     }
     MState<DIM> sc;
     if (!make_state<DIM>(Wc, fc, sc)) return false;
@@ -761,15 +828,15 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     double A0[6], A1[6];
 #pragma unroll
     for (int j = 0; j < 6; j++) {
-        if (STAGE == 0) { A0[j] = Ch[j]; A1[j] = (8.0 * Ch[j] - Cd[j]) * (1.0 / 3.0); }
-        else            { A0[j] = (4.0 / 3.0) * fma(-2.0, Ch[j], Cd[j]); A1[j] = 0.0; }
+        if constexpr (STAGE == 0) { A0[j] = Ch[j]; A1[j] = (8.0 * Ch[j] - Cd[j]) * (1.0 / 3.0); }
+        else                      { A0[j] = (4.0 / 3.0) * fma(-2.0, Ch[j], Cd[j]); A1[j] = 0.0; }
     }
 
     double acc0[NV], acc1[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         acc0[k] = fma(A0[0], M1[k], A0[2] * M3[k]);
-        acc1[k] = fma(A1[0], M1[k], A1[2] * M3[k]);
+        if constexpr (STAGE == 0) acc1[k] = fma(A1[0], M1[k], A1[2] * M3[k]);
     }
     if (tau != 0.0) {
         // (abar1 u + abar2 v) g0 term: Pi'(Wc) Wcx + Sigma'(Wc) Wcy
@@ -778,7 +845,7 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
 #pragma unroll
         for (int k = 0; k < NV; k++) {
             acc0[k] = fma(A0[1], M2[k], acc0[k]);
-            acc1[k] = fma(A1[1], M2[k], acc1[k]);
+            if constexpr (STAGE == 0) acc1[k] = fma(A1[1], M2[k], acc1[k]);
         }
         // Prandtl-number fix (an extension: the paper's BGK flux has Pr = 1).  The energy flux
         // gains (1/Pr - 1) q, q the time-integrated heat flux of the distribution of Eq. (10)
@@ -798,31 +865,30 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
             Qh[2] = fma(-sc.U, lWt, dotv<NV>(lv, M3));
         }
         // non-equilibrium initial parts: left state over u > 0, right state over u < 0, with the
-        // time slope A from the compatibility condition <a1 u + a2 v + A> = 0 (Eq. (9))
+        // time slope A from the compatibility condition <a1 u + a2 v + A> = 0 (Eq. (9)).  The three
+        // terms of the two sides share their time coefficients, so their moments are summed over
+        // the sides first: S4 (g^k), S5 ((a1 u + a2 v) g^k, formed with the equilibrium slopes
+        // above) and S6 (A^k g^k)
+        double S4[NV], S5[NV], S6[NV], D5s[NV], D6s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            S4[k] = pl1[k] + pr1[k]; S5[k] = L5l[k] + L5r[k]; S6[k] = 0.0;
+            if constexpr (PRFIX) { D5s[k] = 0.0; D6s[k] = 0.0; }
+        }
 #pragma unroll
         for (int side = 0; side < 2; side++) {
             const MState<DIM>& st = side == 0 ? sl : sr;
             const Mom<DIM>& mh = side == 0 ? ml : mr;
-            const double* a1 = side == 0 ? a1l : a1r;
-            const double* a2 = side == 0 ? a2l : a2r;
-            const double* L4 = side == 0 ? pl1 : pr1;
-            double Wt[NV], As[NV], L5[NV], L6[NV];
+            double Wt[NV], As[NV], L6[NV];
             w_t<DIM>(st, side == 0 ? Wlx : Wrx, side == 0 ? Wly : Wry, fc.gm1, Wt);
             slope_solve<DIM>(Wt, st, As);
-            Gm<DIM, 2, 0>(a1, mh, L5);
-            if constexpr (DIM == 2) {
-                Gm<DIM, 1, 1>(a2, mh, t1);
-#pragma unroll
-                for (int k = 0; k < NV; k++) L5[k] += t1[k];
-            }
             Gm<DIM, 1, 0>(As, mh, L6);
 #pragma unroll
-            for (int k = 0; k < NV; k++) {
-                acc0[k] = fma(A0[3], L4[k], fma(A0[4], L5[k], fma(A0[5], L6[k], acc0[k])));
-                acc1[k] = fma(A1[3], L4[k], fma(A1[4], L5[k], fma(A1[5], L6[k], acc1[k])));
-            }
+            for (int k = 0; k < NV; k++) S6[k] += L6[k];
             if constexpr (PRFIX) {
-                // density moments of the side's three terms over its half line
+                // density moments of the side's slope terms over its half line
+                const double* a1 = side == 0 ? a1l : a1r;
+                const double* a2 = side == 0 ? a2l : a2r;
                 double D5[NV], D6[NV];
                 Gm<DIM, 1, 0>(a1, mh, D5);
                 if constexpr (DIM == 2) {
@@ -831,18 +897,30 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
                     for (int k = 0; k < NV; k++) D5[k] += t1[k];
                 }
                 Gm<DIM, 0, 0>(As, mh, D6);
-                const double* D4 = side == 0 ? pl0 : pr0;
-                Qh[3] += fma(-sc.U, dotv<NV>(lv, D4), dotv<NV>(lv, L4));
-                Qh[4] += fma(-sc.U, dotv<NV>(lv, D5), dotv<NV>(lv, L5));
-                Qh[5] += fma(-sc.U, dotv<NV>(lv, D6), dotv<NV>(lv, L6));
+#pragma unroll
+                for (int k = 0; k < NV; k++) { D5s[k] += D5[k]; D6s[k] += D6[k]; }
             }
+        }
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            acc0[k] = fma(A0[3], S4[k], fma(A0[4], S5[k], fma(A0[5], S6[k], acc0[k])));
+            if constexpr (STAGE == 0) acc1[k] = fma(A1[3], S4[k], fma(A1[4], S5[k], fma(A1[5], S6[k], acc1[k])));
+        }
+        if constexpr (PRFIX) {
+            // the g^k terms' density moments sum to Wc (Eq. (46))
+            Qh[3] = fma(-sc.U, dotv<NV>(lv, Wc), dotv<NV>(lv, S4));
+            Qh[4] = fma(-sc.U, dotv<NV>(lv, D5s), dotv<NV>(lv, S5));
+            Qh[5] = fma(-sc.U, dotv<NV>(lv, D6s), dotv<NV>(lv, S6));
         }
         if constexpr (PRFIX) {
             double q0 = 0.0, q1 = 0.0;
 #pragma unroll
-            for (int j = 1; j < 6; j++) { q0 = fma(A0[j], Qh[j], q0); q1 = fma(A1[j], Qh[j], q1); }
+            for (int j = 1; j < 6; j++) {
+                q0 = fma(A0[j], Qh[j], q0);
+                if constexpr (STAGE == 0) q1 = fma(A1[j], Qh[j], q1);
+            }
             acc0[NV - 1] = fma(fc.prfix, q0, acc0[NV - 1]);
-            acc1[NV - 1] = fma(fc.prfix, q1, acc1[NV - 1]);
+            if constexpr (STAGE == 0) acc1[NV - 1] = fma(fc.prfix, q1, acc1[NV - 1]);
         }
     }
 #pragma unroll
