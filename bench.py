@@ -13,14 +13,23 @@ With --gpus N > 1 (launched under torchrun) every rank advances its own
 independent replica (the solves do not exchange data) and the value is the
 aggregate over ranks divided by the maximum time over ranks.
 
-The default line also carries "served": a small seeded burst of mixed 1D/2D solves
-through the continuous-batching server against the same requests one at a time
-(throughput, p50/p99 latency, bitwise equality of the results); --no-served skips it.
+The default line also carries
+  "served":  the served configuration's size ranges (1D shock tubes up to 8192 cells, 2D
+             Riemann / vortex up to 1024^2, 2D Navier-Stokes shock tubes up to 2048 x 1024,
+             150 GB budget; 20 seeded requests) through the continuous-batching server against
+             the same requests one at a time: capacities on the seeded burst, p50 / p99
+             latency on the same arrivals stretched to 70 % of the plain capacity measured in
+             the same run, bitwise equality of every result (--no-served skips it);
+  "batched": the 256-solve batched configuration against one solve per launch set, with 5
+             timed steps per solve (--batched-steps; --no-batched skips it).
 Other workloads (--workload batched | served | recon_cost | ns_tube | vortex) print
 their own line.
 
+The roofline is FP64-ALU bound: the numerator counts the algorithmic FP64 work (fixed
+counts, see FLUX_ALG_FLOP_PER_GP), the peak is measured on the GPU by hgks_probe_fp64.
+
 --impl reference times the CPU oracle (the plain FP64 restatement of the
-paper's method) on the host cores, on a bounded sample of the same workload.
+paper's method) on the host cores, on the same 1024^2 problem.
 """
 from __future__ import annotations
 
@@ -44,19 +53,36 @@ UNIT = "Mcell-stage/s"
 N_SIDE = 1024
 WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS, S2O4"
 
-# FP64 operations per Gauss-point flux evaluation of the 2D kernel with tau > 0, counted by
-# ncu as DADD + DMUL + 2 x DFMA thread instructions per Gauss point (512^2 four-quadrant
-# Riemann step; identical per Gauss point at any grid size): first stage 1665.6, second 1616.4.
-FLUX_FLOP_PER_GP_2D = (1665.6 + 1616.4) / 2
+# Algorithmic FP64 work of the step (add / sub, mul, div, sqrt, exp and erfc count one each, fma
+# two), kept fixed here so that the yardstick does not move when a kernel changes:
+# * the flux per Gauss point: the closed form of the flux kernel (2D Euler, tau > 0), counted on
+#   the host by paper_2304_05572_gb300/flopcount.py: 1433 operations in the first stage (F(dt/2)
+#   and the F^n + dt/6 dF^n combination), 1389 in the second;
+# * the rest of the step per cell-stage (indicator, reconstruction, update, time step), counted on
+#   the oracle by oracle/opcount.py on the first step of the 1024^2 problem (the oracle evaluates
+#   these formulas as the paper prints them): every cell smooth 2721.3, every cell troubled
+#   19486.7, the hybrid step 3525.5 at its troubled fraction 0.41 %; a run at another troubled
+#   fraction f moves the hybrid figure along the troubled-minus-smooth slope.  (The oracle's own
+#   flux integrates every moment literally, ORACLE_FLUX_FLOP_PER_GP operations, five times the
+#   closed form: a roofline on that count would exceed the peak, so the flux enters with its
+#   closed-form count.)
+FLUX_ALG_FLOP_PER_GP = (1433.0 + 1389.0) / 2
+ORACLE_FLUX_FLOP_PER_GP = 7025.0
+NONFLUX_FLOP_PER_CELL_STAGE = {"linear": 2721.3, "wenoao": 19486.7, "hybrid": 3525.5,
+                               "hybrid_troubled_fraction": 0.004106}
 # DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.0 and 113.8 MB first stage, 106.9
 # and 107.8 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
 # them: Gauss-point states in, per-Gauss-point fluxes out).
 FLUX_DRAM_BYTES_PER_GP = (113.03e6 + 113.80e6 + 106.85e6 + 107.77e6) / 4 / (2 * 512 * 513)
-# FP64 flop of one whole S2O4 step per cell-stage (all kernels, ncu DADD + DMUL + 2 x DFMA
-# over the 40 launches of one 512^2 four-quadrant step, troubled fraction 1.1 %).
-STEP_FLOP_PER_CELL_STAGE = 8477.8
-# Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (the 1.25 TFLOP/s nominal rate) x 2.07 GHz.
-FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+
+
+def algorithmic_flop_per_cell_stage(n, troubled_fraction):
+    """Algorithmic FP64 work per cell-stage of the n^2 hybrid step at the given troubled
+    fraction: the oracle's count of everything but the flux, plus the closed-form flux of the
+    2 sweeps x 2 Gauss points of every interface."""
+    t = NONFLUX_FLOP_PER_CELL_STAGE
+    rest = t["hybrid"] + (troubled_fraction - t["hybrid_troubled_fraction"]) * (t["wenoao"] - t["linear"])
+    return rest + 4.0 * (n + 1) / n * FLUX_ALG_FLOP_PER_GP
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -182,18 +208,18 @@ def run_reference(args, rank, world):
     return 0
 
 
-def bench_batched(args, torch, hgks, P):
+def run_batched(torch, hgks, P, n_solves, steps, warmup):
     """Independent four-quadrant Riemann solves (sides log-uniform in [64, 1024]): one
     launch set per solve (serial on one stream) against shared batched launches (CUDA
     graph replay, autotuned block sizes).  Both forms advance every solve by the same
     steps from the same state and must give the same bits.  A solve whose state turns
     non-physical (the scheme has no positivity limiter) stops in both forms at the same
-    step; the work counted is the cell-stages actually advanced."""
-    cases = P.batched_workload(args.solves)
+    step; the work counted is the cell-stages actually advanced.  Returns the figures."""
+    cases = P.batched_workload(n_solves)
     stream = torch.cuda.Stream()
     solvers = [hgks.Solver(cfg, stream=stream) for cfg, _ in cases]
     ncell = [int(np.prod(W.shape[1:])) for _, W in cases]
-    warm = max(args.warmup, 4)          # the autotuner takes 4 steps
+    warm = max(warmup, 4)          # the autotuner takes 4 steps
 
     def reset():
         for s, (cfg, W) in zip(solvers, cases):
@@ -216,7 +242,7 @@ def bench_batched(args, torch, hgks, P):
     for s in solvers:
         s.hgks_step(1e9, warm, wait=False)
     s0 = steps_now()
-    t_plain = timed(lambda: [s.hgks_step(1e9, args.steps, wait=False) for s in solvers])
+    t_plain = timed(lambda: [s.hgks_step(1e9, steps, wait=False) for s in solvers])
     s1 = steps_now()
     plain_final = [s.hgks_get_state() for s in solvers]
     work_plain = sum(c * 2 * (b - a) for c, a, b in zip(ncell, s0, s1))
@@ -227,7 +253,7 @@ def bench_batched(args, torch, hgks, P):
     batch.hgks_batch_step(te, nsteps=warm, graph=True, autotune=True)
     batch.hgks_batch_sync()
     b0 = steps_now()
-    t_batch = timed(lambda: batch.hgks_batch_step(te, nsteps=args.steps, graph=True))
+    t_batch = timed(lambda: batch.hgks_batch_step(te, nsteps=steps, graph=True))
     _, failed = batch.hgks_batch_sync()
     b1 = steps_now()
     work_batch = sum(c * 2 * (b - a) for c, a, b in zip(ncell, b0, b1))
@@ -237,55 +263,92 @@ def bench_batched(args, torch, hgks, P):
     batch.hgks_batch_destroy()
     for s in solvers:
         s.hgks_destroy_solver()
-    line = {"metric": METRIC, "workload": "batched: %d four-quadrant Riemann solves, sides log-uniform 64..1024 "
+    return {"workload": "batched: %d four-quadrant Riemann solves, sides log-uniform 64..1024 "
             "(PCG64 seed %d), %d cells in all, %d timed S2O4 steps each after %d untimed"
-            % (len(cases), P.BATCH_SEED, sum(ncell), args.steps, warm),
+            % (len(cases), P.BATCH_SEED, sum(ncell), steps, warm),
             "unit": UNIT, "value": work_batch / t_batch / 1e6, "plain_value": work_plain / t_plain / 1e6,
             "speedup_vs_plain": (work_batch / t_batch) / (work_plain / t_plain),
-            "batched_ms_per_step": t_batch / args.steps * 1e3, "plain_ms_per_step": t_plain / args.steps * 1e3,
+            "batched_ms_per_step": t_batch / steps * 1e3, "plain_ms_per_step": t_plain / steps * 1e3,
             "cell_stages_timed": work_batch, "failed_solves": failed, "bitwise_equal_to_plain": bool(same),
             "autotuned_block_sizes": tpb, "l2": "working set (%.1f GB of state) far above L2" % (
-                sum(ncell) * 4 * 8 * 3 / 1e9), "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+                sum(ncell) * 4 * 8 * 3 / 1e9)}
+
+
+def bench_batched(args, torch, hgks, P):
+    """The batched workload as its own JSON line."""
+    d = run_batched(torch, hgks, P, args.solves, args.steps, args.warmup)
+    line = {"metric": METRIC, **d, "dtype": "f64", "data": "synthetic", "higher_is_better": True}
     print(json.dumps(line), flush=True)
 
 
-def run_served(torch, P, requests, rate, max_1d, max_2d, max_ns, budget_gb, steps_per_iter):
-    """Seeded Poisson stream of mixed solves through the continuous-batching server, and
-    the same trace served one solve at a time (FIFO, each solve alone on the GPU).
-    Returns the figures as a dict."""
+def _fifo_latencies(trace, dur):
+    """Latency of each request when the requests are served one at a time in arrival order
+    (FIFO), each taking its measured solo duration."""
+    clock, lat = 0.0, {}
+    for r in sorted(trace, key=lambda r: r["arrival"]):
+        clock = max(clock, r["arrival"]) + dur[r["id"]]
+        lat[r["id"]] = clock - r["arrival"]
+    return lat
+
+
+def run_served(torch, P, requests, rate, max_1d, max_2d, max_ns, budget_gb, steps_per_iter, load=0.7):
+    """A seeded Poisson stream of mixed solves (1D shock tubes, 2D Riemann / vortex, 2D
+    Navier-Stokes shock tubes) through the continuous-batching server against the same
+    requests served one at a time (FIFO, each solve alone on the GPU).
+
+    1. Plain arm: every request alone, in order; its solo duration and result are kept.
+    2. Burst: the seeded arrivals at `rate` (every request queued within a second) through the
+       server: the served and plain throughputs (work / wall) are the two capacities.
+    3. Load-scaled: the same arrivals stretched so that the offered load is `load` times the
+       plain capacity measured in step 1 (rate = load x requests / total solo time); the
+       served latencies against the FIFO latencies of the plain arm on the same arrivals.
+    Every served result must equal the request solved alone, bit for bit."""
     from paper_2304_05572_gb300 import server
     trace = P.served_trace(n_requests=requests, rate=rate, max_1d=max_1d, max_2d=max_2d, max_ns=max_ns)
     stream = torch.cuda.Stream()
-    srv = server.Server(budget_bytes=budget_gb * 1e9, stream=stream, steps_per_iter=steps_per_iter,
-                        autotune=False)
-    res = srv.run(trace)
-    served_wall = srv.wall
-    lat = np.array([res[r["id"]]["latency"] for r in trace])
-    work = sum(res[r["id"]]["cells"] * 2 * res[r["id"]]["steps"] for r in trace)
-    # plain: FIFO, one solve at a time, each alone
-    t0 = time.perf_counter()
-    done_at = {}
-    same = True
-    clock = 0.0
+    dur, alone, work = {}, {}, {}
     for r in trace:
-        start = max(clock, r["arrival"])
         w0 = time.perf_counter()
         out, st = server.run_alone(r, stream=stream)
-        dur = time.perf_counter() - w0
-        clock = start + dur
-        done_at[r["id"]] = clock - r["arrival"]
-        same = same and np.array_equal(out, res[r["id"]]["W"])
-    plain_wall = time.perf_counter() - t0
-    plain_lat = np.array([done_at[r["id"]] for r in trace])
-    return {"workload": "served: %d requests, Poisson rate %.1f/s (PCG64 seed %d), mix of 1D shock "
-            "tubes <= %d cells, 2D Riemann/vortex <= %d^2, 2D NS shock tubes <= %dx%d, t_end ~ U[0.05, 0.3], "
-            "budget %.0f GB" % (len(trace), rate, P.SERVE_SEED, max_1d, max_2d, max_ns, max_ns // 2, budget_gb),
-            "unit": UNIT, "value": work / served_wall / 1e6, "plain_value": work / plain_wall / 1e6,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "plain_p50_latency_s": float(np.percentile(plain_lat, 50)),
-            "plain_p99_latency_s": float(np.percentile(plain_lat, 99)),
-            "served_wall_s": served_wall, "plain_wall_s": plain_wall, "iterations": srv.iterations,
-            "peak_resident_solves": srv.peak_resident, "results_bitwise_equal_alone": bool(same)}
+        dur[r["id"]] = time.perf_counter() - w0
+        alone[r["id"]] = out
+        work[r["id"]] = int(np.prod(np.shape(r["W"])[1:])) * 2 * int(st["steps"])
+    total_work, total_dur = float(sum(work.values())), float(sum(dur.values()))
+
+    def serve(tr):
+        srv = server.Server(budget_bytes=budget_gb * 1e9, stream=stream, steps_per_iter=steps_per_iter,
+                            autotune=False)
+        res = srv.run(tr)
+        lat = np.array([res[r["id"]]["latency"] for r in tr])
+        same = all(np.array_equal(res[r["id"]]["W"], alone[r["id"]]) for r in tr)
+        return srv, lat, same
+
+    srv_b, lat_b, same_b = serve(trace)
+    plain_b = np.array([v for v in _fifo_latencies(trace, dur).values()])
+    lam = load * len(trace) / total_dur
+    scaled = [dict(r, arrival=r["arrival"] * rate / lam) for r in trace]
+    srv_l, lat_l, same_l = serve(scaled)
+    plain_l = np.array([v for v in _fifo_latencies(scaled, dur).values()])
+    pct = lambda a, q: float(np.percentile(a, q))
+    return {"workload": "served: %d requests (PCG64 seed %d), mix of 1D shock tubes 256..%d cells, 2D Riemann/vortex "
+            "64..%d^2, 2D NS shock tubes 128x64..%dx%d (Re ~ U[200, 2000]), t_end ~ U[0.05, 0.3], budget %.0f GB"
+            % (len(trace), P.SERVE_SEED, max_1d, max_2d, max_ns, max_ns // 2, budget_gb),
+            "unit": UNIT, "cell_stages": total_work,
+            # burst: capacities
+            "value": total_work / srv_b.wall / 1e6, "plain_value": total_work / total_dur / 1e6,
+            "burst": {"rate_per_s": rate, "served_wall_s": srv_b.wall, "plain_wall_s": total_dur,
+                      "p50_latency_s": pct(lat_b, 50), "p99_latency_s": pct(lat_b, 99),
+                      "plain_p50_latency_s": pct(plain_b, 50), "plain_p99_latency_s": pct(plain_b, 99),
+                      "iterations": srv_b.iterations, "peak_resident_solves": srv_b.peak_resident},
+            # load-scaled: latency at the same offered load
+            "load_scaled": {"offered_load_of_plain_capacity": load, "rate_per_s": lam,
+                            "served_wall_s": srv_l.wall,
+                            "p50_latency_s": pct(lat_l, 50), "p99_latency_s": pct(lat_l, 99),
+                            "plain_p50_latency_s": pct(plain_l, 50), "plain_p99_latency_s": pct(plain_l, 99),
+                            "iterations": srv_l.iterations, "peak_resident_solves": srv_l.peak_resident},
+            "p50_latency_s": pct(lat_l, 50), "p99_latency_s": pct(lat_l, 99),
+            "plain_p50_latency_s": pct(plain_l, 50), "plain_p99_latency_s": pct(plain_l, 99),
+            "results_bitwise_equal_alone": bool(same_b and same_l)}
 
 
 def bench_served(args, torch, hgks, P):
@@ -406,7 +469,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-served", action="store_true", help="skip the small served-vs-plain run of the default line")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain part of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched part of the default line")
+    ap.add_argument("--served-requests", type=int, default=20, help="requests of the default line's served part")
+    ap.add_argument("--batched-steps", type=int, default=5, help="timed steps of the default line's batched part")
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ref-side", type=int, default=N_SIDE, help="grid side of the reference arm's problem")
     ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube", "vortex"])
@@ -414,11 +480,11 @@ def main():
     ap.add_argument("--vortex-n", type=int, default=800, help="vortex: cells per side")
     ap.add_argument("--recon-cases", default="", help="comma-separated subset of the recon_cost cases")
     ap.add_argument("--solves", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=20)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--max-1d", type=int, default=4096)
-    ap.add_argument("--max-2d", type=int, default=512)
-    ap.add_argument("--max-ns", type=int, default=512)
+    ap.add_argument("--max-1d", type=int, default=8192)
+    ap.add_argument("--max-2d", type=int, default=1024)
+    ap.add_argument("--max-ns", type=int, default=2048)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--steps-per-iter", type=int, default=8)
     args = ap.parse_args()
@@ -520,28 +586,44 @@ def main():
     e2e_value = replica_throughput(world, cells, e2e_steps, e2e_s)
     state_bytes = int(W0.nbytes)
 
-    # ---- dominant kernel roofline (FP64 ALU)
+    # ---- FP64 peak of this GPU: the DFMA rate per clock measured by the probe (with the clock
+    # sampled while it runs), at the median clock of the timed region
+    clocks = clk.summary()
+    with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0) as clkp:
+        probe_tflops, probe_ms, n_sm = hgks.hgks_probe_fp64(stream)
+    probe_mhz = clkp.summary()["sm_mhz"] or clocks["sm_mhz"]
+    run_mhz = clocks["sm_mhz"] or probe_mhz
+    peak_tflops = probe_tflops * (run_mhz / probe_mhz) if (run_mhz and probe_mhz) else probe_tflops
+    derived = n_sm * 4 * (run_mhz or 0.0) / 1e6   # SMs x 4 FP64 flop/clk (2 DFMA issues) x clock
+
+    # ---- dominant kernel roofline (FP64 ALU) on the algorithmic count
     flux_ms, flux_calls = timing.get("gks_flux", (0.0, 0))
     launches = int(stats.get("launches", 0)) - launches0     # kernels of the timed steps only
     roofline = None
     if flux_calls:
         avg_ms = flux_ms / flux_calls
         gp_per_launch = 2 * (n + 1) * n          # Gauss points of one sweep
-        if FLUX_FLOP_PER_GP_2D:
-            achieved = FLUX_FLOP_PER_GP_2D * gp_per_launch / (avg_ms * 1e-3) / 1e12
-            roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                        "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
-                        "traffic": FLUX_DRAM_BYTES_PER_GP * gp_per_launch if n == N_SIDE else None,
-                        "kernel": "gks_flux", "avg_launch_ms": avg_ms,
-                        "peak_note": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (1.25 TFLOP/s nominal)"}
-        else:
-            roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                        "frac": None, "traffic": None, "kernel": "gks_flux", "avg_launch_ms": avg_ms}
+        achieved = FLUX_ALG_FLOP_PER_GP * gp_per_launch / (avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops,
+                    "traffic": FLUX_DRAM_BYTES_PER_GP * gp_per_launch if n == N_SIDE else None,
+                    "kernel": "gks_flux", "avg_launch_ms": avg_ms,
+                    "flop_per_launch": FLUX_ALG_FLOP_PER_GP * gp_per_launch,
+                    "unit_of_work": "Gauss-point flux: %.0f algorithmic FP64 operations (closed form; "
+                                    "the oracle's literal moment integration takes %.0f)"
+                                    % (FLUX_ALG_FLOP_PER_GP, ORACLE_FLUX_FLOP_PER_GP),
+                    "peak_note": "measured: hgks_probe_fp64 (DFMA chains, 64 warps per SM on %d SMs) after the "
+                                 "timed region, %.3f TFLOP/s at %s MHz (%.2f FP64 flop/clk/SM), taken at the "
+                                 "timed region's %s MHz; nominal from the SM count and that clock: %.3f TFLOP/s"
+                                 % (n_sm, probe_tflops, probe_mhz, probe_tflops * 1e6 / (n_sm * probe_mhz)
+                                    if probe_mhz else float("nan"), run_mhz, derived)}
     shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in timing.values())), 4) for k, v in timing.items() if v[1]}
-    if roofline is not None:
-        step_tflops = STEP_FLOP_PER_CELL_STAGE * value / world * 1e6 / 1e12
-        roofline["whole_step"] = {"flop_per_cell_stage": STEP_FLOP_PER_CELL_STAGE, "achieved": step_tflops,
-                                  "frac": step_tflops / (FP64_PEAK_GFLOPS / 1e3), "unit": "TFLOP/s"}
+    if roofline is not None and NONFLUX_FLOP_PER_CELL_STAGE["hybrid"] is not None:
+        fpcs = algorithmic_flop_per_cell_stage(n, float(troubled))
+        step_tflops = fpcs * value / world * 1e6 / 1e12
+        roofline["whole_step"] = {"flop_per_cell_stage": fpcs, "achieved": step_tflops,
+                                  "frac": step_tflops / peak_tflops, "unit": "TFLOP/s",
+                                  "troubled_fraction": float(troubled)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_timed,
@@ -561,16 +643,23 @@ def main():
         # is the whole step, those included)
         "value_without_dt_and_ghost": value / max(1e-9, 1.0 - shares.get("dt", 0.0) - shares.get("ghost", 0.0)
                                                   - shares.get("misc", 0.0)),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "wall_s_timed": t_wall,
     }
     if rank == 0 and world == 1 and not args.no_served:
-        # the metric's served-vs-plain part: a small burst of mixed solves through the server
-        # and the same requests one at a time (both bitwise equal), with p50 / p99 latency
+        # the metric's served-vs-plain part on the served configuration's size ranges: capacity
+        # (burst) and p50 / p99 latency at 70 % of the plain capacity, results bitwise equal
         try:
-            line["served"] = run_served(torch, P, 16, 200.0, 2048, 256, 256, 150.0, 8)
+            line["served"] = run_served(torch, P, args.served_requests, 200.0, 8192, 1024, 2048, 150.0,
+                                        args.steps_per_iter)
         except Exception as e:  # pragma: no cover
             line["served"] = {"failed": str(e)}
+    if rank == 0 and world == 1 and not args.no_batched:
+        # the batched configuration (256 solves) with a reduced number of timed steps
+        try:
+            line["batched"] = run_batched(torch, hgks, P, 256, args.batched_steps, 4)
+        except Exception as e:  # pragma: no cover
+            line["batched"] = {"failed": str(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             v, secs, cores = cpu_oracle_rate(N_SIDE, 1)

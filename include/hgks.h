@@ -228,8 +228,9 @@ void hgks_batch_destroy(hgks_batch* b);
 /* ------------------------------------------------------------------------ */
 
 /* Measure the FP64 fused-multiply-add rate of the current device: 8 blocks of
- * 256 threads per SM each run 8 independent DFMA chains (4 launches, CUDA
- * events on `stream`, NULL = default stream; the call waits for them).
+ * 256 threads per SM each run 8 independent DFMA chains (4 launches of about
+ * 70 ms each at the nominal rate, CUDA events on `stream`, NULL = default
+ * stream; the call waits for them).
  * *tflops = 2 x DFMA per second / 1e12 (the FP64 peak every kernel of the
  * step is measured against), *ms (may be NULL) the time of the 4 launches,
  * *sms (may be NULL) the device's SM count.  Errors: HGKS_EINVAL (tflops NULL),

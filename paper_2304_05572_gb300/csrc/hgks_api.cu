@@ -706,7 +706,7 @@ extern "C" int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sm
     if (!tflops) return HGKS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int nsm = device_sm_count();
-    const int blocks = nsm * 8, iters = 4096;      // 8 blocks of 256 threads per SM: 64 warps
+    const int blocks = nsm * 8, iters = 16384;     // 8 blocks of 256 threads per SM: 64 warps, ~0.3 s
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);

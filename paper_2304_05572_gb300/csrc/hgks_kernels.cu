@@ -8,6 +8,7 @@
 //   compacted the same way) -> dense WENO-AO pass] -> gas-kinetic flux per Gauss point
 // -> stage update.  dt is reduced, clipped to t_end and applied on the device.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdio>
 
@@ -841,9 +842,17 @@ static cudaEvent_t take_event(hgks_solver* s)
     return e;
 }
 
+// NVTX range around the enqueue of one kernel class (named as in kclass_names), so that a
+// timeline tool attributes the launches to their class; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <typename F>
 static void timed(hgks_solver* s, int cls, int nkernels, F&& launch)
 {
+    NvtxRange range(kclass_names[cls]);
     s->launches += nkernels;
     if (!s->timing) { launch(); return; }
     cudaEvent_t a = take_event(s), b = take_event(s);
@@ -913,6 +922,7 @@ static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
 template <int DIM>
 static void enqueue_stage(hgks_solver* s, int stage)
 {
+    NvtxRange range(stage == 0 ? "S2O4 stage 1" : "S2O4 stage 2");
     const Params& P = s->P;
     cudaStream_t st = s->stream;
     double* Win = stage == 0 ? s->W : s->Ws;
@@ -933,6 +943,7 @@ static void enqueue_stage(hgks_solver* s, int stage)
 
 cudaError_t launch_step(hgks_solver* s, double t_end)
 {
+    NvtxRange range("hgks_step");
     const Params& P = s->P;
     cudaStream_t st = s->stream;
     double tol = 1e-12 * (fabs(t_end) > 1.0 ? fabs(t_end) : 1.0);
@@ -1025,6 +1036,7 @@ void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* 
 cudaError_t batch_enqueue_step(const BatchPlan& plan, const SolveDesc* dd, const int* dboff, const double* dtend,
                                cudaStream_t st, cudaEvent_t* ev)
 {
+    NvtxRange range("hgks_batch_step");
     const int n = plan.n;
     const int dim = plan.dim;
     auto bo = [&](int c) { return dboff + (size_t)c * (n + 1); };
