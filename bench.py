@@ -397,6 +397,32 @@ def bench_single(args, torch, hgks, P):
     print(json.dumps(line), flush=True)
 
 
+def bench_ns_wall(args, torch, hgks, P):
+    """The viscous shock tube of Sec. 3.6 as the paper runs it (Re = 200, Pr = 1, 500 x 250 cells,
+    CFL 0.3, t = 1): the density along the bottom wall (the cell row next to it) at t = 1, with
+    the run's time, steps and wall time."""
+    nx = args.ns_nx
+    cfg, W, t_end = P.viscous_shock_tube(nx, nx // 2, Re=200.0, prandtl=1.0)
+    stream = torch.cuda.Stream()
+    s = hgks.Solver(cfg, stream=stream)
+    s.hgks_set_state(np.ascontiguousarray(W))
+    t0 = time.perf_counter()
+    n = s.hgks_step(t_end, 1 << 30)
+    wall = time.perf_counter() - t0
+    Wf = s.hgks_get_state()
+    st = s.hgks_get_stats()
+    s.hgks_destroy_solver()
+    dx = 1.0 / nx
+    line = {"metric": "bottom-wall density of the viscous shock tube (Sec. 3.6)",
+            "workload": "2D NS viscous shock tube, %dx%d, Re 200, Pr 1, CFL 0.3, hybrid, S2O4, to t = %g"
+                        % (nx, nx // 2, t_end),
+            "t": st["t"], "steps": n, "status": int(st["status"]), "wall_s": wall,
+            "troubled_fraction": float(st["troubled"].sum()) / max(1, int(st["examined"].sum())),
+            "x_first_centre": 0.5 * dx, "dx": dx, "rho_wall": [float(v) for v in Wf[0, 0, :]],
+            "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 RECON_CLASSES = ("raw_normal_flags", "normal_recon", "normal_weno_ao", "raw_tangential_flags", "tangential_recon",
                  "tangential_weno_ao")
 
@@ -475,8 +501,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=5, help="timed steps of the default line's batched part")
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ref-side", type=int, default=N_SIDE, help="grid side of the reference arm's problem")
-    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube", "vortex"])
-    ap.add_argument("--ns-nx", type=int, default=1000, help="ns_tube: cells along x (ny = nx/2)")
+    ap.add_argument("--workload", default="riemann1024", choices=["riemann1024", "batched", "served", "recon_cost", "ns_tube", "vortex", "ns_wall"])
+    ap.add_argument("--ns-nx", type=int, default=1000, help="ns_tube / ns_wall: cells along x (ny = nx/2)")
     ap.add_argument("--vortex-n", type=int, default=800, help="vortex: cells per side")
     ap.add_argument("--recon-cases", default="", help="comma-separated subset of the recon_cost cases")
     ap.add_argument("--solves", type=int, default=256)
@@ -518,6 +544,8 @@ def main():
         return bench_recon_cost(args, torch, hgks, P)
     if args.workload in ("ns_tube", "vortex"):
         return bench_single(args, torch, hgks, P)
+    if args.workload == "ns_wall":
+        return bench_ns_wall(args, torch, hgks, P)
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
