@@ -231,8 +231,7 @@ void hgks_batch_destroy(hgks_batch* b);
  * 256 threads per SM each run 8 independent DFMA chains (4 launches of about
  * 70 ms each at the nominal rate, CUDA events on `stream`, NULL = default
  * stream; the call waits for them).
- * *tflops = 2 x DFMA per second / 1e12 (the FP64 peak every kernel of the
- * step is measured against), *ms (may be NULL) the time of the 4 launches,
+ * *tflops = 2 x DFMA per second / 1e12, *ms (may be NULL) the time of the 4 launches,
  * *sms (may be NULL) the device's SM count.  Errors: HGKS_EINVAL (tflops NULL),
  * HGKS_ECUDA (message in hgks_last_error(NULL)). */
 int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms);
