@@ -340,6 +340,8 @@ __global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* 
 }
 
 
+// One troubled side per aligned group of 4 lanes (weno_ao_face_x4: lane q carries characteristic
+// field q); `start`, `stride` count lane groups.  Lane r stores component r.
 template <int NV>
 __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
 {
@@ -348,6 +350,8 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
+    const int q = threadIdx.x & 3;
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
     for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
         uint32_t it = S.itemsN[i];
         int side = it & 1;
@@ -355,7 +359,7 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
         int m = (int)(lm % S.nm), L = (int)(lm / S.nm);
         int t = L + S.tlo;
         int c = m - 1 + side;
-        double Qw[5][NV], Qs[NV], val[NV], d[NV], der[NV];
+        double Qw[5][NV], Qs[NV], val[NV], d[NV];
         const double* base = cellp(P, S, W, t, c - 2);
 #pragma unroll
         for (int s = 0; s < 5; s++)
@@ -368,21 +372,29 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
             long long o = (long long)S.perm[k] * P.g.plane;
             Qs[k] = ((ex(ld(cl + o)) + ex(ld(cr + o))) * ex(0.5)).v;
         }
-        weno_ao_face<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, val, d);
-#pragma unroll
-        for (int k = 0; k < NV; k++) der[k] = (ex(d[k]) * ex(S.inv_hn)).v;
+        weno_ao_face_x4<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, gmask, val, d);
+        double vq = 0.0, dq = 0.0;
         if (nonphysical<NV>(P.gamma, val)) {
+            vq = Qw[2][q < NV ? q : 0];
+        } else {
 #pragma unroll
-            for (int k = 0; k < NV; k++) { val[k] = Qw[2][k]; der[k] = 0.0; }
+            for (int k = 0; k < NV; k++)
+                if (k == q) { vq = val[k]; dq = (ex(d[k]) * ex(S.inv_hn)).v; }
         }
-        store_line<NV>(P, S, L, m, side, val, der);
+        if (q < NV) {
+            long long plane = (long long)S.nlines * S.nm;
+            long long o = (long long)L * S.nm + m;
+            S.line[(long long)(side * NV + q) * plane + o] = vq;
+            S.line[(long long)((2 + side) * NV + q) * plane + o] = dq;
+        }
     }
 }
 
 template <int NV>
 __global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
 {
-    b_normal_ao<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    b_normal_ao<NV>(P, S, W, ctrl, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2,
+                    ((long long)gridDim.x * blockDim.x) >> 2);
 }
 
 
@@ -492,6 +504,8 @@ __global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
 }
 
 
+// One troubled tangential pass per aligned group of 4 lanes (tang_ao_x4); `start`, `stride` count
+// lane groups.  Lane r stores component r of both Gauss points.
 __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
 {
     if (ctrl->done) return;
@@ -499,13 +513,15 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
+    const int q = threadIdx.x & 3;
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
     for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
         uint32_t it = S.itemsT[i];
         int X = it & 3;
         long long tm = it >> 2;
         int m = (int)(tm % S.nm), t = (int)(tm / S.nm);
         // tangential outputs feed only the flux: free-order arithmetic (fx), FMA contraction allowed
-        fx qs[4], Lm[4][4], Rm[4][4], Uc[5][4];
+        fx qs[4], Lm[4][4], Rm[4][4], x[5][4];
         const double* cl = cellp(P, S, W, t, m - 1);
         const double* cr = cellp(P, S, W, t, m);
 #pragma unroll
@@ -515,38 +531,32 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
         }
         eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
 #pragma unroll
-        for (int s = 0; s < 5; s++) {
-            fx x[4];
+        for (int s = 0; s < 5; s++)
 #pragma unroll
-            for (int k = 0; k < 4; k++) x[k] = fx(lineval(S, X, k, t - 2 + s, m));
-            matvec<4>(Lm, x, Uc[s]);
-        }
-        double cv[4][2], cd[4][2];
+            for (int k = 0; k < 4; k++) x[s][k] = fx(lineval(S, X, k, t - 2 + s, m));
+        double v[4][2], d[4][2];
+        tang_ao_x4(Lm, Rm, x, ak, gmask, v, d);
+        gp_positivity(P, S, t, m, X, v, d);
+        // component q of both Gauss points (layout of store_gp)
+        long long plane = (long long)S.nt * S.nm;
+        long long o = (long long)t * S.nm + m;
+        int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            fx q[5];
+            if (k != q) continue;
 #pragma unroll
-            for (int s = 0; s < 5; s++) q[s] = Uc[s][k];
-            gauss_ao(q, ak, cv[k], cd[k]);
-        }
-        double v[4][2], d[4][2];
-#pragma unroll
-        for (int g = 0; g < 2; g++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                double a = 0.0, b = 0.0;
-#pragma unroll
-                for (int c = 0; c < 4; c++) { a = fma(Rm[r][c].v, cv[c][g], a); b = fma(Rm[r][c].v, cd[c][g], b); }
-                v[r][g] = a; d[r][g] = b;
+            for (int g = 0; g < 2; g++) {
+                S.gp[(long long)((g * 6 + qv) * 4 + k) * plane + o] = v[k][g];
+                if (X <= 1) S.gp[(long long)((g * 6 + qv + 2) * 4 + k) * plane + o] = d[k][g] * S.inv_ht;
             }
-        gp_positivity(P, S, t, m, X, v, d);
-        store_gp(S, t, m, X, v, d, S.inv_ht);
+        }
     }
 }
 
 __global__ void k_tang_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
 {
-    b_tang_ao(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    b_tang_ao(P, S, W, ctrl, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2,
+              ((long long)gridDim.x * blockDim.x) >> 2);
 }
 
 
@@ -759,7 +769,7 @@ template <int NV>
 __global__ void kb_normal_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
 {
     HGKS_BATCH_BLOCK();
-    b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
+    b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id >> 2, (nblk_ * blockDim.x) >> 2);
 }
 
 __global__ void kb_raw_tflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
@@ -777,7 +787,7 @@ __global__ void kb_tang(const SolveDesc* __restrict__ D, const int* __restrict__
 __global__ void kb_tang_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
 {
     HGKS_BATCH_BLOCK();
-    b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
+    b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id >> 2, (nblk_ * blockDim.x) >> 2);
 }
 
 template <int DIM, int STAGE>
@@ -880,7 +890,7 @@ static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
         k_normal<NV><<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, Win, ctrl, stage);
     });
     timed(s, KC_NORMAL_AO, 1, [&] {
-        long long maxn = (long long)S.nlines * S.nm * 2;
+        long long maxn = (long long)S.nlines * S.nm * 2 * 4;     // 4 lanes per item
         unsigned int b = blocks_for(maxn, 128);
         if (b > (unsigned)(sms * 8)) b = sms * 8;
         k_normal_ao<NV><<<b, 128, 0, st>>>(P, S, Win, ctrl);
@@ -895,7 +905,7 @@ static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
             k_tang<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl, stage);
         });
         timed(s, KC_TANG_AO, 1, [&] {
-            long long maxn = (long long)S.nt * S.nm * 4;
+            long long maxn = (long long)S.nt * S.nm * 4 * 4;     // 4 lanes per item
             unsigned int b = blocks_for(maxn, 128);
             if (b > (unsigned)(sms * 8)) b = sms * 8;
             k_tang_ao<<<b, 128, 0, st>>>(P, S, Win, ctrl);
@@ -1017,10 +1027,10 @@ void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* 
                 case BK_GHY: b = dim == 2 ? blocks_for((long long)g.nv * (g.nx + 2 * NG) * NG * 2, t) : 0; break;
                 case BK_RAWN: b = sweep_used ? blocks_for((long long)S.nlines * (S.nn + 4), t) : 0; break;
                 case BK_NORMAL: b = sweep_used ? blocks_for((long long)S.nlines * S.nm, t) : 0; break;
-                case BK_NAO: b = sweep_used ? blocks_for((long long)S.nlines * S.nm * 2, t * 8) : 0; break;
+                case BK_NAO: b = sweep_used ? blocks_for((long long)S.nlines * S.nm * 2 * 4, t * 8) : 0; break;
                 case BK_RAWT: b = dim == 2 ? blocks_for((long long)(S.nt + 2) * S.nm, t) : 0; break;
                 case BK_TANG: b = dim == 2 ? blocks_for((long long)S.nt * S.nm, t) : 0; break;
-                case BK_TAO: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * 4, t * 8) : 0; break;
+                case BK_TAO: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * 4 * 4, t * 8) : 0; break;
                 case BK_FLUX: b = sweep_used ? blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t) : 0; break;
                 case BK_UPD: b = blocks_for(cells, t); break;
             }

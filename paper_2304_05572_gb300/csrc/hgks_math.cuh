@@ -286,6 +286,57 @@ __device__ __forceinline__ void weno_ao_face(double gam, const AOConst& k, const
     for (int c = 0; c < NV; c++) { val[c] = v[c].v; der[c] = d[c].v; }
 }
 
+// The characteristic WENO-AO face reconstruction of weno_ao_face, spread over the 4 lanes of an
+// aligned lane group (lane q = threadIdx.x & 3): lane q projects the window onto characteristic
+// field q (row q of L), runs the nonlinear weights and the AO combination of that field alone,
+// and the 4 fields' results are exchanged with shuffles for the projection back with R.  Every
+// value is formed by the same operations in the same order as in weno_ao_face, so the result
+// (returned in every lane) is bit-identical; the per-lane work, and so the latency of an item
+// on the narrow FP64 pipe, is about a quarter.  Lanes q >= NV (1D) duplicate field NV-1.
+// All 4 lanes of the group must call this together (mask gmask).
+template <int NV>
+__device__ __forceinline__ void weno_ao_face_x4(double gam, const AOConst& k, const double (*Qw)[NV], const double* Qs,
+                                                int side, unsigned gmask, double* val, double* der)
+{
+    const int q = threadIdx.x & 3;
+    const int qc = q < NV ? q : NV - 1;
+    const int lane0 = threadIdx.x & 28;
+    ex L[NV][NV], R[NV][NV], qs[NV];
+#pragma unroll
+    for (int c = 0; c < NV; c++) qs[c] = ex(Qs[c]);
+    eigvec<NV>(gam, qs, 1.0, 0.0, L, R);
+    ex Lq[NV];
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        ex v = L[0][c];
+#pragma unroll
+        for (int r = 1; r < NV; r++) v = qc == r ? L[r][c] : v;
+        Lq[c] = v;
+    }
+    ex u[5], wb[4], pv[4], pd[4];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        ex s = Lq[0] * ex(Qw[j][0]) + Lq[1] * ex(Qw[j][1]);
+#pragma unroll
+        for (int c = 2; c < NV; c++) s = s + Lq[c] * ex(Qw[j][c]);
+        u[j] = s;
+    }
+    ao_weights(u, k, wb);
+    face_polys(u, side, pv, pd);
+    const double uvq = ao_combine(wb, k, pv).v, udq = ao_combine(wb, k, pd).v;
+    ex uv[NV], ud[NV];
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        uv[c] = ex(__shfl_sync(gmask, uvq, lane0 + c));
+        ud[c] = ex(__shfl_sync(gmask, udq, lane0 + c));
+    }
+    ex v[NV], d[NV];
+    matvec<NV>(R, uv, v);
+    matvec<NV>(R, ud, d);
+#pragma unroll
+    for (int c = 0; c < NV; c++) { val[c] = v[c].v; der[c] = d[c].v; }
+}
+
 // Reading (no safeguard is printed): rho <= 0 or p <= 0 after reconstruction -> first order.
 // For rho > 0 (and gamma > 1), p > 0 exactly when rho E - ke > 0, ke = 0.5 (m_x^2 + m_y^2);
 // tested in that division-free form, in this order.
@@ -359,6 +410,48 @@ __device__ __forceinline__ void gauss_ao(const fx* q, const AOConst& k, double* 
         a = fma(ws[s], pa, a); b = fma(ws[s], pb, b); e = fma(ws[s], pe, e); f = fma(ws[s], pf, f);
     }
     v[0] = a; v[1] = b; d[0] = e; d[1] = f;
+}
+
+// Tangential WENO-AO of one pass (4 components) at the two Gauss points, spread over the 4 lanes
+// of an aligned lane group like weno_ao_face_x4: lane q projects the 5 line values onto field q
+// (row q of Lm), runs gauss_ao for it, and the fields' Gauss-point values and derivatives are
+// exchanged with shuffles; every lane returns the 4 conservative components v[r][g], d[r][g]
+// after the projection back with Rm.  Free-order arithmetic (the outputs only feed the flux).
+__device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4], const fx (*x)[4], const AOConst& ak,
+                                           unsigned gmask, double (*v)[2], double (*d)[2])
+{
+    const int q = threadIdx.x & 3;
+    const int lane0 = threadIdx.x & 28;
+    fx Lq[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        fx w = Lm[0][c];
+#pragma unroll
+        for (int r = 1; r < 4; r++) w = q == r ? Lm[r][c] : w;
+        Lq[c] = w;
+    }
+    fx u[5];
+#pragma unroll
+    for (int s = 0; s < 5; s++) u[s] = ((Lq[0] * x[s][0] + Lq[1] * x[s][1]) + Lq[2] * x[s][2]) + Lq[3] * x[s][3];
+    double cvq[2], cdq[2];
+    gauss_ao(u, ak, cvq, cdq);
+    double cv[4][2], cd[4][2];
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+            cv[c][g] = __shfl_sync(gmask, cvq[g], lane0 + c);
+            cd[c][g] = __shfl_sync(gmask, cdq[g], lane0 + c);
+        }
+#pragma unroll
+    for (int g = 0; g < 2; g++)
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            double a = 0.0, b = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) { a = fma(Rm[r][c].v, cv[c][g], a); b = fma(Rm[r][c].v, cd[c][g], b); }
+            v[r][g] = a; d[r][g] = b;
+        }
 }
 
 // ---------------------------------------------------------------- gas-kinetic flux
