@@ -6,9 +6,10 @@ device memory its solver needs (hgks_footprint_bytes) fits in the budget;
 admitted solves keep their state resident on the device and advance together:
 every iteration issues one batched group of S2O4 steps (hgks_batch_step, CUDA
 graph replay) per dimension for all resident solves, the 1D and 2D groups on
-their own streams so that they overlap on the device, and newly admitted solves
-join the ones already running.  A solve retires at its end time, when its
-state turned non-physical (the scheme has no positivity limiter; the status is
+their own streams so that they overlap on the device (the group of the faster
+dimension takes more steps, so that both take about the same device time), and
+newly admitted solves join the ones already running.  A solve retires at its
+end time, when its state turned non-physical (the scheme has no positivity limiter; the status is
 reported with the result) or when its request is cancelled; its state is
 copied back, its memory freed and its latency (completion minus arrival,
 queueing included) recorded.  A request whose configuration the library
@@ -40,11 +41,14 @@ class GpuBackend:
 
     def __init__(self, stream=None, autotune: bool = False):
         import torch
+        self._torch = torch
         # one stream per dimension: the 1D batch (small, latency-bound launches) overlaps on the
         # device with the 2D batch; `stream`, if given, serves the 2D solves
         self.streams = {1: torch.cuda.Stream(), 2: stream if stream is not None else torch.cuda.Stream()}
         self.autotune = autotune
         self._batches = {}        # dim -> (tuple of handles, Batch)
+        self._events = {}         # dim -> (start, end, nsteps) of the last enqueued group of steps
+        self._ms_per_step = {}    # dim -> device time per batched step of the last group
 
     def footprint(self, cfg) -> int:
         """Device bytes of a solver of cfg; 0 if the library rejects the configuration."""
@@ -70,14 +74,27 @@ class GpuBackend:
         return b
 
     def step(self, dim, handles, t_ends, nsteps):
-        """Enqueue nsteps batched steps of the given solvers (no wait)."""
-        self._batch(dim, handles).hgks_batch_step(t_ends, nsteps=nsteps, graph=True, autotune=self.autotune)
+        """Enqueue nsteps batched steps of the given solvers (no wait), timed by CUDA events."""
+        b = self._batch(dim, handles)
+        st = self.streams[dim]
+        e0, e1 = self._torch.cuda.Event(enable_timing=True), self._torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.hgks_batch_step(t_ends, nsteps=nsteps, graph=True, autotune=self.autotune)
+        e1.record(st)
+        self._events[dim] = (e0, e1, nsteps)
 
     def sync(self, dim):
         """Wait for the dimension's batch; (t, status, steps) per solver in step() order."""
         b = self._batches[dim][1]
         b.hgks_batch_sync()
+        ev = self._events.pop(dim, None)
+        if ev is not None and ev[2] > 0:
+            self._ms_per_step[dim] = ev[0].elapsed_time(ev[1]) / ev[2]
         return list(zip(*b.hgks_batch_status()))
+
+    def ms_per_step(self, dim):
+        """Device time of one batched step of the dimension's last group (None before the first)."""
+        return self._ms_per_step.get(dim)
 
     def fetch(self, handle):
         return handle.hgks_get_state()
@@ -97,6 +114,7 @@ class Server:
         self.budget = float(budget_bytes)
         self.backend = backend if backend is not None else GpuBackend(stream, autotune)
         self.steps_per_iter = int(steps_per_iter)
+        self.max_steps_factor = 16
         self.clock = clock
         self.used = 0.0
         self.active = {}          # id -> dict(req, handle, bytes, t_admit)
@@ -121,6 +139,20 @@ class Server:
         self.backend.release(a["handle"])
         self.used -= a["bytes"]
         self._answer(a["req"], now, status, W=W, t=t, steps=steps, admitted=a["t_admit"])
+
+    def _steps_per_dim(self, by_dim):
+        """Steps of each dimension's group in this iteration: the dimension whose batched step
+        takes longest on the device does steps_per_iter steps, the others as many as fit in the
+        same device time (up to max_steps_factor times more), so that no batch waits idle for
+        the other at the end of an iteration.  Without timings (first iterations, or a backend
+        that reports none) every dimension does steps_per_iter."""
+        ms = {d: getattr(self.backend, "ms_per_step", lambda d: None)(d) for d in by_dim}
+        known = [v for v in ms.values() if v]
+        if len(by_dim) < 2 or len(known) < len(by_dim):
+            return {d: self.steps_per_iter for d in by_dim}
+        budget = self.steps_per_iter * max(known)
+        return {d: max(1, min(self.steps_per_iter * self.max_steps_factor, int(budget / ms[d])))
+                for d in by_dim}
 
     def run(self, trace, time_scale: float = 1.0):
         """Serve a list of requests (dicts with id, arrival [s], cfg, W, t_end and optionally
@@ -164,10 +196,11 @@ class Server:
             by_dim = {}
             for rid, a in self.active.items():
                 by_dim.setdefault(int(a["req"]["cfg"]["dim"]), []).append(rid)
+            nsteps = self._steps_per_dim(by_dim)
             for dim, ids in by_dim.items():             # enqueue every dimension first (they overlap)
                 ids.sort()
                 self.backend.step(dim, [self.active[i]["handle"] for i in ids],
-                                  [self.active[i]["req"]["t_end"] for i in ids], self.steps_per_iter)
+                                  [self.active[i]["req"]["t_end"] for i in ids], nsteps[dim])
             self.iterations += 1
             finished = []
             for dim, ids in by_dim.items():

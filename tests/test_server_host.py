@@ -124,3 +124,37 @@ def test_arrivals_in_the_future_wait_for_their_time():
     res = srv.run(trace)
     assert res[1]["admitted"] >= 0.0005 - 1e-4
     assert all(r["status"] == server.STATUS_OK for r in res.values())
+
+
+class TimedBackend(FakeBackend):
+    """FakeBackend that reports a device time per batched step for each dimension."""
+
+    def __init__(self, clock, ms):
+        super().__init__(clock)
+        self.ms = ms
+        self.requested = []
+
+    def step(self, dim, handles, t_ends, nsteps):
+        self.requested.append((dim, nsteps))
+        super().step(dim, handles, t_ends, nsteps)
+
+    def ms_per_step(self, dim):
+        return self.ms[dim]
+
+
+def test_faster_dimension_takes_more_steps_per_iteration():
+    clock = FakeClock()
+    be = TimedBackend(clock, {1: 0.2, 2: 1.6})
+    srv = server.Server(budget_bytes=1e9, steps_per_iter=4, backend=be, clock=clock)
+    trace = [_req(0, 0.0, 0.5, 0.001, 10, dim=1), _req(1, 0.0, 0.5, 0.01, 10, dim=2)]
+    res = srv.run(trace)
+    assert all(r["status"] == 0 for r in res.values())
+    first = {}
+    for dim, n in be.requested:
+        first.setdefault(dim, n)
+    assert first == {2: 4, 1: 32}            # 1.6 ms per 2D step x 4 steps = 32 1D steps of 0.2 ms
+    # with one dimension resident only, the plain steps_per_iter applies
+    be2 = TimedBackend(FakeClock(), {1: 0.2, 2: 1.6})
+    srv2 = server.Server(budget_bytes=1e9, steps_per_iter=4, backend=be2, clock=be2.clock)
+    srv2.run([_req(0, 0.0, 0.2, 0.01, 10, dim=1)])
+    assert {n for _, n in be2.requested} == {4}
