@@ -286,6 +286,7 @@ __device__ __forceinline__ void weno_ao_face(double gam, const AOConst& k, const
     for (int c = 0; c < NV; c++) { val[c] = v[c].v; der[c] = d[c].v; }
 }
 
+#if defined(__CUDACC__)   // lane-group functions: device code only (the host count compiles the flux alone)
 // The characteristic WENO-AO face reconstruction of weno_ao_face, spread over the 4 lanes of an
 // aligned lane group (lane q = threadIdx.x & 3): lane q projects the window onto characteristic
 // field q (row q of L), runs the nonlinear weights and the AO combination of that field alone,
@@ -336,6 +337,7 @@ __device__ __forceinline__ void weno_ao_face_x4(double gam, const AOConst& k, co
 #pragma unroll
     for (int c = 0; c < NV; c++) { val[c] = v[c].v; der[c] = d[c].v; }
 }
+#endif
 
 // Reading (no safeguard is printed): rho <= 0 or p <= 0 after reconstruction -> first order.
 // For rho > 0 (and gamma > 1), p > 0 exactly when rho E - ke > 0, ke = 0.5 (m_x^2 + m_y^2);
@@ -412,6 +414,7 @@ __device__ __forceinline__ void gauss_ao(const fx* q, const AOConst& k, double* 
     v[0] = a; v[1] = b; d[0] = e; d[1] = f;
 }
 
+#if defined(__CUDACC__)
 // Tangential WENO-AO of one pass (4 components) at the two Gauss points, spread over the 4 lanes
 // of an aligned lane group like weno_ao_face_x4: lane q projects the 5 line values onto field q
 // (row q of Lm), runs gauss_ao for it, and the fields' Gauss-point values and derivatives are
@@ -453,6 +456,7 @@ __device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4],
             v[r][g] = a; d[r][g] = b;
         }
 }
+#endif
 
 // ---------------------------------------------------------------- gas-kinetic flux
 // Moments of a Maxwellian: u^n on one half line times the density (n <= 6), normalised v^m
