@@ -224,6 +224,19 @@ const char* hgks_batch_last_error(const hgks_batch* b);
 void hgks_batch_destroy(hgks_batch* b);
 
 /* ------------------------------------------------------------------------ */
+/* Debug build (the paper has no counterpart).                               */
+/* ------------------------------------------------------------------------ */
+
+/* A library built with HGKS_DEBUG_BOUNDS (paper_2304_05572_gb300/_build.py, debug=True:
+ * _lib/libhgks_debug.so) checks every global-memory load and store of its kernels against
+ * the range of the solver's device buffers; an access outside it is skipped (a load returns
+ * 0) and counted, and the address of the first one is kept; no kernel traps.  Returns 1 and
+ * the process-wide *count and *first_address (0 if none) in a debug build, 0 (both set to 0)
+ * in the normal build.  Waits for the device.  Errors: HGKS_EINVAL (NULL argument),
+ * HGKS_ECUDA. */
+int hgks_debug_bounds(unsigned long long* count, unsigned long long* first_address);
+
+/* ------------------------------------------------------------------------ */
 /* FP64 rate probe (measurement helper; the paper has no counterpart).       */
 /* ------------------------------------------------------------------------ */
 

@@ -139,6 +139,9 @@ void fill_sweeps(const hgks_config* c, const Params& P, Sweep* sw)
         S.nt = c->dim == 2 ? (d == 0 ? g.ny : g.nx) : 1;
         S.nm = S.nn + 1;
         S.nlines = c->dim == 2 ? S.nt + 6 : 1;
+        // below ~4 warps per scheduler of segments, spread a segment over 4 lanes (shorter FP64
+        // chains per thread); the results do not depend on the choice
+        S.tlanes = (long long)S.nt * S.nm < 65536 ? 4 : 1;
         S.tlo = c->dim == 2 ? -3 : 0;
         S.sN = d == 0 ? 1 : g.pitch;
         S.sT = d == 0 ? g.pitch : 1;
@@ -259,6 +262,8 @@ extern "C" int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_sol
         cudaFree(s->pool); delete s; return HGKS_ENOMEM;
     }
     char* base = (char*)s->pool;
+    s->P.g.lo = base;
+    s->P.g.hi = base + L.total;
     s->W = (double*)(base + L.off_W);
     s->Ws = (double*)(base + L.off_Ws);
     s->Acc = (double*)(base + L.off_Acc);
@@ -276,6 +281,8 @@ extern "C" int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_sol
             S.itemsT = (uint32_t*)(base + L.off_itemsT[d]);
         }
         S.flux = (double*)(base + L.off_flux[d]);
+        S.lo = base;
+        S.hi = base + L.total;
     }
     memset(s->cap, 0, sizeof(s->cap));
     s->capture = 0;
@@ -700,6 +707,16 @@ extern "C" int hgks_batch_info(const hgks_batch* b, int* tpb, int cap, long long
 extern "C" const char* hgks_batch_last_error(const hgks_batch* b) { return b ? b->err : g_create_err; }
 
 // ---------------------------------------------------------------------------
+// Debug build: out-of-range accesses the kernels skipped.
+extern "C" int hgks_debug_bounds(unsigned long long* count, unsigned long long* first_address)
+{
+    if (!count || !first_address) return HGKS_EINVAL;
+    int r = debug_bounds_read(count, first_address);
+    if (r < 0) { set_err(g_create_err, "hgks_debug_bounds: reading the counters failed"); return HGKS_ECUDA; }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 rate of the current device (the denominator of the benchmark's roofline).
 extern "C" int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms)
 {
@@ -801,6 +818,8 @@ extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, dou
     s.timing = 0;
     s.err[0] = 0;
     char* b = (char*)base;
+    s.P.g.lo = b;
+    s.P.g.hi = b + L.total;
     s.W = (double*)(b + L.off_W);
     s.Ws = (double*)(b + L.off_Ws);
     s.Acc = (double*)(b + L.off_Acc);
@@ -818,6 +837,8 @@ extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, dou
             S.itemsT = (uint32_t*)(b + L.off_itemsT[d]);
         }
         S.flux = (double*)(b + L.off_flux[d]);
+        S.lo = b;
+        S.hi = b + L.total;
     }
     const GridGeom& g = s.P.g;
     // the array keeps the previous call's contents: start every call from zero

@@ -36,6 +36,8 @@ struct GridGeom {
     long long plane;           // pitch * rows
     long long origin;          // offset of interior cell (0, 0)
     double dx, dy;
+    const char* lo;            // the solver's device buffers: [lo, hi) (checked by the debug build)
+    const char* hi;
 };
 
 // One sweep in its local frame: n = index normal to the interfaces, t = tangential index.
@@ -44,6 +46,7 @@ struct Sweep {
     int nn, nt;                // cells normal / tangential
     int nm;                    // interfaces per line (nn + 1)
     int nlines;                // lines with normal reconstruction (nt + 6 in 2D, 1 in 1D)
+    int tlanes;                // lanes per segment of the tangential kernels: 4 for small sweeps, else 1
     int tlo;                   // first line index (-3 in 2D, 0 in 1D)
     long long sN, sT;          // state strides for +1 in n / t
     int perm[4];               // local component -> global component
@@ -57,6 +60,8 @@ struct Sweep {
     double* flux;              // [ngp][2][nv][nt][nm] per-Gauss-point flux outputs (global order)
     uint32_t* itemsN;          // AO work list, normal pass
     uint32_t* itemsT;          // AO work list, tangential passes
+    const char* lo;            // the solver's device buffers: [lo, hi) (checked by the debug build)
+    const char* hi;
 };
 
 struct Params {
@@ -135,6 +140,9 @@ extern const char* kclass_names[KC_COUNT];
 cudaError_t launch_step(hgks_solver* s, double t_end);
 cudaError_t launch_set_time(hgks_solver* s, double t0);
 int device_sm_count();
+// the debug build's count of out-of-range accesses and the first such address (returns 1), or 0
+// without the checks compiled in, -1 if the device read failed
+int debug_bounds_read(unsigned long long* count, unsigned long long* first);
 // FP64 rate probe: `blocks` blocks of 256 threads, 8 DFMA chains of `iters` steps per thread
 cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters);
 

@@ -25,7 +25,37 @@ namespace {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+// Global-memory access.  Every load and store of a kernel names the range its pointer must lie
+// in (R.lo, R.hi: the solver's device buffers).  The debug build (HGKS_DEBUG_BOUNDS) checks each
+// access against that range: an access outside it is skipped (a load returns 0), counted, and
+// the address of the first one is kept for hgks_debug_bounds; nothing traps.  The normal build
+// accesses memory directly.
+#ifdef HGKS_DEBUG_BOUNDS
+__device__ unsigned long long g_dbg_count;
+__device__ unsigned long long g_dbg_first;
+template <class T>
+__device__ __forceinline__ bool in_range(const T* p, const char* lo, const char* hi)
+{
+    const char* c = (const char*)p;
+    if (c >= lo && c + sizeof(T) <= hi) return true;
+    atomicAdd(&g_dbg_count, 1ull);
+    atomicCAS(&g_dbg_first, 0ull, (unsigned long long)(uintptr_t)c);
+    return false;
+}
+template <class T, class R>
+__device__ __forceinline__ T ldc(const T* p, const R& r) { return in_range(p, r.lo, r.hi) ? __ldg(p) : T(0); }
+template <class T, class R>
+__device__ __forceinline__ T rdc(const T* p, const R& r) { return in_range(p, r.lo, r.hi) ? *p : T(0); }
+template <class T, class V, class R>
+__device__ __forceinline__ void stc(T* p, V v, const R& r) { if (in_range(p, r.lo, r.hi)) *p = (T)v; }
+#else
+template <class T, class R>
+__device__ __forceinline__ T ldc(const T* p, const R&) { return __ldg(p); }
+template <class T, class R>
+__device__ __forceinline__ T rdc(const T* p, const R&) { return *p; }
+template <class T, class V, class R>
+__device__ __forceinline__ void stc(T* p, V v, const R&) { *p = (T)v; }
+#endif
 
 // ---------------------------------------------------------------- ghost cells
 // x ghosts on interior rows, then y ghosts over the padded width (fills corners).
@@ -60,18 +90,18 @@ __device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ 
     int bc = P.bc[side];
     int dst = side == 0 ? -l : g.nx - 1 + l;
     double* base = W + g.origin + (long long)k * g.plane + (long long)j * g.pitch;
-    if (bc == HGKS_BC_INFLOW) { base[dst] = P.bc_state[side][k]; return; }
+    if (bc == HGKS_BC_INFLOW) { stc(base + dst, P.bc_state[side][k], g); return; }
     int src;
     bool mirror = bc == HGKS_BC_REFLECT || bc == HGKS_BC_SYMMETRY || bc == HGKS_BC_NOSLIP;
     if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.nx - l : l - 1;
     else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.nx - 1;
     else src = side == 0 ? l - 1 : g.nx - l;
-    double v = base[src];
+    double v = rdc(base + src, g);
     if (mirror) {
         if (k == 1) v = -v;
         if (bc == HGKS_BC_NOSLIP && g.dim == 2 && k == 2) v = -v;
     }
-    base[dst] = v;
+    stc(base + dst, v, g);
 }
 
 __global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
@@ -94,16 +124,16 @@ __device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ 
     int bc = P.bc[2 + side];
     int dst = side == 0 ? -l : g.ny - 1 + l;
     double* base = W + g.origin + (long long)k * g.plane + i;
-    if (bc == HGKS_BC_INFLOW) { base[(long long)dst * g.pitch] = P.bc_state[2 + side][k]; return; }
+    if (bc == HGKS_BC_INFLOW) { stc(base + (long long)dst * g.pitch, P.bc_state[2 + side][k], g); return; }
     if (bc == HGKS_BC_SHOCK_TRACK) {
         const double xc = cell_centre(P.x0, i, g.dx), yc = cell_centre(P.y0, dst, g.dy);
         const double t = stage_time(ctrl, stage);
         const double xs = (ex(P.shock_x0) + ex(P.shock_cot) * (ex(yc) + ex(P.shock_speed) * ex(t))).v;
-        base[(long long)dst * g.pitch] = xc < xs ? P.bc_state[2 + side][k] : P.shock_pre[k];
+        stc(base + (long long)dst * g.pitch, xc < xs ? P.bc_state[2 + side][k] : P.shock_pre[k], g);
         return;
     }
     if (bc == HGKS_BC_SHOCK_WALL && cell_centre(P.x0, i, g.dx) < P.shock_x0) {
-        base[(long long)dst * g.pitch] = P.bc_state[2 + side][k];
+        stc(base + (long long)dst * g.pitch, P.bc_state[2 + side][k], g);
         return;
     }
     int src;
@@ -111,12 +141,12 @@ __device__ __forceinline__ void b_ghost_y(const Params& P, double* __restrict__ 
     if (bc == HGKS_BC_PERIODIC) src = side == 0 ? g.ny - l : l - 1;
     else if (bc == HGKS_BC_EXTRAP) src = side == 0 ? 0 : g.ny - 1;
     else src = side == 0 ? l - 1 : g.ny - l;
-    double v = base[(long long)src * g.pitch];
+    double v = rdc(base + (long long)src * g.pitch, g);
     if (mirror) {
         if (k == 2) v = -v;
         if (bc == HGKS_BC_NOSLIP && k == 1) v = -v;
     }
-    base[(long long)dst * g.pitch] = v;
+    stc(base + (long long)dst * g.pitch, v, g);
 }
 
 __global__ void k_ghost_y(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, int stage)
@@ -148,12 +178,12 @@ __device__ __forceinline__ void b_dt(const Params& P, const double* __restrict__
     for (long long id = start; id < n; id += stride) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
         const double* c = W + g.origin + (long long)j * g.pitch + i;
-        ex rho(c[0]);
+        ex rho(rdc(c, g));
         ex ri = ex(1.0) / rho;
-        ex U = ex(c[g.plane]) * ri;
-        ex V = g.dim == 2 ? ex(c[2 * g.plane]) * ri : ex(0.0);
+        ex U = ex(rdc(c + g.plane, g)) * ri;
+        ex V = g.dim == 2 ? ex(rdc(c + 2 * g.plane, g)) * ri : ex(0.0);
         ex q2 = U * U + V * V;
-        ex p = (ex(P.gamma) - ex(1.0)) * (ex(c[(g.nv - 1) * g.plane]) - (ex(0.5) * rho) * q2);
+        ex p = (ex(P.gamma) - ex(1.0)) * (ex(rdc(c + (g.nv - 1) * g.plane, g)) - (ex(0.5) * rho) * q2);
         ex a = xsqrt((ex(P.gamma) * p) * ri);
         ex d = ex(h) / (xsqrt(q2) + a);
         if (P.viscous) {
@@ -217,7 +247,8 @@ __device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned int
 }
 
 // warp-aggregated append of one item per set predicate; returns nothing, writes list
-__device__ __forceinline__ void warp_push(unsigned int* cnt, uint32_t* list, bool pred, uint32_t item)
+template <class R>
+__device__ __forceinline__ void warp_push(unsigned int* cnt, uint32_t* list, bool pred, uint32_t item, const R& rg)
 {
     unsigned int mask = __ballot_sync(0xffffffffu, pred);
     if (!mask) return;
@@ -226,7 +257,7 @@ __device__ __forceinline__ void warp_push(unsigned int* cnt, uint32_t* list, boo
     unsigned int base = 0;
     if (lane == leader) base = atomicAdd(cnt, (unsigned int)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
+    if (pred) stc(list + base + __popc(mask & ((1u << lane) - 1u)), item, rg);
 }
 
 // ---------------------------------------------------------------- normal pass
@@ -253,11 +284,11 @@ __device__ __forceinline__ void b_raw_nflags(const Params& P, const Sweep& S, co
             double q[5];
             const double* b = base + (long long)S.perm[k] * P.g.plane;
 #pragma unroll
-            for (int s = 0; s < 5; s++) q[s] = ld(b + (long long)s * S.sN);
+            for (int s = 0; s < 5; s++) q[s] = ldc(b + (long long)s * S.sN, S);
             tr |= indicator_raw(q, S.Z1n);
         }
     }
-    S.rawN[id] = (uint8_t)tr;
+    stc(S.rawN + id, tr, S);
 }
 
 template <int NV>
@@ -274,8 +305,8 @@ __device__ __forceinline__ void store_line(const Params& P, const Sweep& S, int 
     long long o = (long long)L * S.nm + m;
 #pragma unroll
     for (int k = 0; k < NV; k++) {
-        S.line[(long long)(side * NV + k) * plane + o] = val[k];
-        S.line[(long long)((2 + side) * NV + k) * plane + o] = der[k];
+        stc(S.line + (long long)(side * NV + k) * plane + o, val[k], S);
+        stc(S.line + (long long)((2 + side) * NV + k) * plane + o, der[k], S);
     }
 }
 
@@ -297,12 +328,12 @@ __device__ __forceinline__ void b_normal(const Params& P, const Sweep& S, const 
             int f;
             if (P.recon_mode == HGKS_RECON_LINEAR) f = 0;
             else if (P.recon_mode == HGKS_RECON_WENOAO) f = 1;
-            else f = raw[c + 1] | raw[c + 2] | raw[c + 3];          // Step 4
+            else f = rdc(raw + c + 1, S) | rdc(raw + c + 2, S) | rdc(raw + c + 3, S);   // Step 4
             fl[side] = f;
         }
         uint8_t* fo = S.flagN + (long long)L * (S.nn + 2);
-        fo[m + 1] = (uint8_t)fl[1];
-        if (m == 0) fo[0] = (uint8_t)fl[0];
+        stc(fo + m + 1, fl[1], S);
+        if (m == 0) stc(fo, fl[0], S);
     }
     bool counted = active && t >= 0 && t < S.nt && m < S.nn;
     warp_count(&ctrl->troubled[stage][S.dir][0], counted && fl[1] ? 1u : 0u);
@@ -310,7 +341,7 @@ __device__ __forceinline__ void b_normal(const Params& P, const Sweep& S, const 
 #pragma unroll
     for (int side = 0; side < 2; side++) {
         bool push = active && fl[side];
-        warp_push(&ctrl->cnt[S.dir][0], S.itemsN, push, (uint32_t)((((long long)L * S.nm + m) << 1) | side));
+        warp_push(&ctrl->cnt[S.dir][0], S.itemsN, push, (uint32_t)((((long long)L * S.nm + m) << 1) | side), S);
         if (!active || fl[side]) continue;
         int c = m - 1 + side;
         double val[NV], der[NV];
@@ -320,14 +351,14 @@ __device__ __forceinline__ void b_normal(const Params& P, const Sweep& S, const 
             double q[5];
             const double* b = base + (long long)S.perm[k] * P.g.plane;
 #pragma unroll
-            for (int s = 0; s < 5; s++) q[s] = ld(b + (long long)s * S.sN);
+            for (int s = 0; s < 5; s++) q[s] = ldc(b + (long long)s * S.sN, S);
             if (side == 0) linear_left(q, S.inv12hn, val[k], der[k]);
             else linear_right(q, S.inv12hn, val[k], der[k]);
         }
         if (nonphysical<NV>(P.gamma, val)) {
             const double* cc = cellp(P, S, W, t, c);
 #pragma unroll
-            for (int k = 0; k < NV; k++) { val[k] = ld(cc + (long long)S.perm[k] * P.g.plane); der[k] = 0.0; }
+            for (int k = 0; k < NV; k++) { val[k] = ldc(cc + (long long)S.perm[k] * P.g.plane, S); der[k] = 0.0; }
         }
         store_line<NV>(P, S, L, m, side, val, der);
     }
@@ -353,7 +384,7 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
     const int q = threadIdx.x & 3;
     const unsigned gmask = 0xFu << (threadIdx.x & 28);
     for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
-        uint32_t it = S.itemsN[i];
+        uint32_t it = rdc(S.itemsN + i, S);
         int side = it & 1;
         long long lm = it >> 1;
         int m = (int)(lm % S.nm), L = (int)(lm / S.nm);
@@ -364,13 +395,13 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
 #pragma unroll
         for (int s = 0; s < 5; s++)
 #pragma unroll
-            for (int k = 0; k < NV; k++) Qw[s][k] = ld(base + (long long)s * S.sN + (long long)S.perm[k] * P.g.plane);
+            for (int k = 0; k < NV; k++) Qw[s][k] = ldc(base + (long long)s * S.sN + (long long)S.perm[k] * P.g.plane, S);
         const double* cl = cellp(P, S, W, t, m - 1);
         const double* cr = cellp(P, S, W, t, m);
 #pragma unroll
         for (int k = 0; k < NV; k++) {
             long long o = (long long)S.perm[k] * P.g.plane;
-            Qs[k] = ((ex(ld(cl + o)) + ex(ld(cr + o))) * ex(0.5)).v;
+            Qs[k] = ((ex(ldc(cl + o, S)) + ex(ldc(cr + o, S))) * ex(0.5)).v;
         }
         weno_ao_face_x4<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, gmask, val, d);
         double vq = 0.0, dq = 0.0;
@@ -384,8 +415,8 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
         if (q < NV) {
             long long plane = (long long)S.nlines * S.nm;
             long long o = (long long)L * S.nm + m;
-            S.line[(long long)(side * NV + q) * plane + o] = vq;
-            S.line[(long long)((2 + side) * NV + q) * plane + o] = dq;
+            stc(S.line + (long long)(side * NV + q) * plane + o, vq, S);
+            stc(S.line + (long long)((2 + side) * NV + q) * plane + o, dq, S);
         }
     }
 }
@@ -402,10 +433,38 @@ __global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, con
 __device__ __forceinline__ double lineval(const Sweep& S, int X, int k, int t, int m)
 {
     long long plane = (long long)S.nlines * S.nm;
-    return ld(S.line + (long long)(X * 4 + k) * plane + (long long)(t - S.tlo) * S.nm + m);
+    return ldc(S.line + (long long)(X * 4 + k) * plane + (long long)(t - S.tlo) * S.nm + m, S);
 }
 
-__device__ __forceinline__ void b_raw_tflags(const Params& P, const Sweep& S, const Ctrl* __restrict__ ctrl, long long id)
+// Raw tangential flags, one segment per aligned group of 4 lanes: lane q runs the indicator of
+// every pass X on component q, the 4 components' bits are OR-ed with shuffles (a cell is smooth
+// only if every component is), and lane 0 stores them.  `id` counts lanes.
+__device__ __forceinline__ void b_raw_tflags_x4(const Params& P, const Sweep& S, const Ctrl* __restrict__ ctrl, long long id)
+{
+    if (ctrl->done) return;
+    long long total = (long long)(S.nt + 2) * S.nm;
+    const long long seg = id >> 2;
+    if (seg >= total) return;                       // the same for the 4 lanes of a group
+    const int q = (int)(id & 3);
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
+    int m = (int)(seg % S.nm);
+    int t = (int)(seg / S.nm) - 1;
+    unsigned int bits = 0;
+    if (P.recon_mode == HGKS_RECON_HYBRID) {
+#pragma unroll
+        for (int X = 0; X < 4; X++) {
+            double qv[5];
+#pragma unroll
+            for (int s = 0; s < 5; s++) qv[s] = lineval(S, X, q, t - 2 + s, m);
+            bits |= (unsigned)indicator_raw(qv, S.Z1t) << X;
+        }
+        bits |= __shfl_xor_sync(gmask, bits, 1);
+        bits |= __shfl_xor_sync(gmask, bits, 2);
+    }
+    if (q == 0) stc(S.rawT + seg, bits, S);
+}
+
+__device__ __forceinline__ void b_raw_tflags_x1(const Params& P, const Sweep& S, const Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
     long long total = (long long)(S.nt + 2) * S.nm;
@@ -427,7 +486,16 @@ __device__ __forceinline__ void b_raw_tflags(const Params& P, const Sweep& S, co
             bits |= (uint8_t)(tr << X);
         }
     }
-    S.rawT[id] = bits;
+    stc(S.rawT + id, bits, S);
+}
+
+// Small sweeps (fewer segments than a few warps per scheduler) spread a segment over 4 lanes,
+// which shortens the chain of FP64 instructions per thread; large sweeps keep one segment per
+// thread.  The arithmetic, and so every result, is the same either way.
+__device__ __forceinline__ void b_raw_tflags(const Params& P, const Sweep& S, const Ctrl* __restrict__ ctrl, long long id)
+{
+    if (S.tlanes == 4) b_raw_tflags_x4(P, S, ctrl, id);
+    else b_raw_tflags_x1(P, S, ctrl, id);
 }
 
 __global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
@@ -435,21 +503,6 @@ __global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
     b_raw_tflags(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-
-__device__ __forceinline__ void store_gp(const Sweep& S, int t, int m, int X, const double (*v)[2], const double (*d)[2], double inv_ht)
-{
-    long long plane = (long long)S.nt * S.nm;
-    long long o = (long long)t * S.nm + m;
-    // Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry
-    int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
-#pragma unroll
-    for (int g = 0; g < 2; g++)
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            S.gp[(long long)((g * 6 + qv) * 4 + k) * plane + o] = v[k][g];
-            if (X <= 1) S.gp[(long long)((g * 6 + qv + 2) * 4 + k) * plane + o] = d[k][g] * inv_ht;
-        }
-}
 
 __device__ __forceinline__ void gp_positivity(const Params& P, const Sweep& S, int t, int m, int X, double (*v)[2], double (*d)[2])
 {
@@ -464,7 +517,81 @@ __device__ __forceinline__ void gp_positivity(const Params& P, const Sweep& S, i
     }
 }
 
-__device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ctrl, int stage, long long id)
+// Gauss-point reconstruction of the smooth passes, one segment per aligned group of 4 lanes, lane q
+// carrying component q: the Step-4 spread flags of the segment (the same in every lane; lane 0
+// stores them, counts them and appends the troubled passes to the WENO-AO work list), then for
+// every smooth pass the quartic of component q at both Gauss points; the positivity test of the
+// Q^l, Q^r passes gathers the 4 components with shuffles.  `id` counts lanes.  Every lane of the
+// warp reaches the warp-wide counts and appends.
+__device__ __forceinline__ void b_tang_x4(const Params& P, const Sweep& S, Ctrl* ctrl, int stage, long long id)
+{
+    if (ctrl->done) return;
+    long long total = (long long)S.nt * S.nm;
+    const long long seg = id >> 2;
+    const int q = (int)(id & 3);
+    const int lane0 = threadIdx.x & 28;
+    const unsigned gmask = 0xFu << lane0;
+    bool active = seg < total;                      // the same for the 4 lanes of a group
+    int m = 0, t = 0;
+    unsigned int bits = 0;
+    if (active) {
+        m = (int)(seg % S.nm); t = (int)(seg / S.nm);
+        if (P.recon_mode == HGKS_RECON_LINEAR) bits = 0;
+        else if (P.recon_mode == HGKS_RECON_WENOAO) bits = 0xF;
+        else bits = rdc(S.rawT + (long long)t * S.nm + m, S) | rdc(S.rawT + (long long)(t + 1) * S.nm + m, S)
+                    | rdc(S.rawT + (long long)(t + 2) * S.nm + m, S);
+        if (q == 0) stc(S.flagT + seg, bits, S);
+    }
+    const bool lead = active && q == 0;
+    warp_count(&ctrl->troubled[stage][S.dir][1], lead ? (unsigned)__popc(bits) : 0u);
+    warp_count(&ctrl->examined[stage][S.dir][1], lead ? 4u : 0u);
+    const long long plane = (long long)S.nt * S.nm;
+    const long long o = (long long)t * S.nm + m;
+#pragma unroll
+    for (int X = 0; X < 4; X++) {
+        bool f = active && ((bits >> X) & 1);
+        warp_push(&ctrl->cnt[S.dir][1], S.itemsT, f && q == 0, (uint32_t)((seg << 2) | X), S);
+        if (!active || f) continue;                 // the same for the 4 lanes of a group
+        double qv[5], v[2], d[2];
+#pragma unroll
+        for (int s = 0; s < 5; s++) qv[s] = lineval(S, X, q, t - 2 + s, m);
+        gauss_linear(qv, v, d);
+        if (X <= 1) {
+            // Reading: a reconstructed state with rho <= 0 or p <= 0 falls back to first order
+#pragma unroll
+            for (int g = 0; g < 2; g++) {
+                double Q[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) Q[c] = __shfl_sync(gmask, v[g], lane0 + c);
+                if (nonphysical<4>(P.gamma, Q)) { v[g] = lineval(S, X, q, t, m); d[g] = 0.0; }
+            }
+        }
+        // Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry
+        constexpr int qx[4] = {0, 3, 1, 4};
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+            stc(S.gp + (long long)((g * 6 + qx[X]) * 4 + q) * plane + o, v[g], S);
+            if (X <= 1) stc(S.gp + (long long)((g * 6 + qx[X] + 2) * 4 + q) * plane + o, d[g] * S.inv_ht, S);
+        }
+    }
+}
+
+__device__ __forceinline__ void store_gp(const Sweep& S, int t, int m, int X, const double (*v)[2], const double (*d)[2], double inv_ht)
+{
+    long long plane = (long long)S.nt * S.nm;
+    long long o = (long long)t * S.nm + m;
+    // Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry
+    int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
+#pragma unroll
+    for (int g = 0; g < 2; g++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            stc(S.gp + (long long)((g * 6 + qv) * 4 + k) * plane + o, v[k][g], S);
+            if (X <= 1) stc(S.gp + (long long)((g * 6 + qv + 2) * 4 + k) * plane + o, d[k][g] * inv_ht, S);
+        }
+}
+
+__device__ __forceinline__ void b_tang_x1(const Params& P, const Sweep& S, Ctrl* ctrl, int stage, long long id)
 {
     if (ctrl->done) return;
     long long total = (long long)S.nt * S.nm;
@@ -475,15 +602,16 @@ __device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ct
         m = (int)(id % S.nm); t = (int)(id / S.nm);
         if (P.recon_mode == HGKS_RECON_LINEAR) bits = 0;
         else if (P.recon_mode == HGKS_RECON_WENOAO) bits = 0xF;
-        else bits = S.rawT[(long long)t * S.nm + m] | S.rawT[(long long)(t + 1) * S.nm + m] | S.rawT[(long long)(t + 2) * S.nm + m];
-        S.flagT[id] = (uint8_t)bits;
+        else bits = rdc(S.rawT + (long long)t * S.nm + m, S) | rdc(S.rawT + (long long)(t + 1) * S.nm + m, S)
+                    | rdc(S.rawT + (long long)(t + 2) * S.nm + m, S);
+        stc(S.flagT + id, bits, S);
     }
     warp_count(&ctrl->troubled[stage][S.dir][1], active ? (unsigned)__popc(bits) : 0u);
     warp_count(&ctrl->examined[stage][S.dir][1], active ? 4u : 0u);
 #pragma unroll
     for (int X = 0; X < 4; X++) {
         bool f = active && ((bits >> X) & 1);
-        warp_push(&ctrl->cnt[S.dir][1], S.itemsT, f, (uint32_t)((((long long)t * S.nm + m) << 2) | X));
+        warp_push(&ctrl->cnt[S.dir][1], S.itemsT, f, (uint32_t)((((long long)t * S.nm + m) << 2) | X), S);
         if (!active || f) continue;
         double v[4][2], d[4][2];
 #pragma unroll
@@ -496,6 +624,12 @@ __device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ct
         gp_positivity(P, S, t, m, X, v, d);
         store_gp(S, t, m, X, v, d, S.inv_ht);
     }
+}
+
+__device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ctrl, int stage, long long id)
+{
+    if (S.tlanes == 4) b_tang_x4(P, S, ctrl, stage, id);
+    else b_tang_x1(P, S, ctrl, stage, id);
 }
 
 __global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
@@ -516,7 +650,7 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
     const int q = threadIdx.x & 3;
     const unsigned gmask = 0xFu << (threadIdx.x & 28);
     for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
-        uint32_t it = S.itemsT[i];
+        uint32_t it = rdc(S.itemsT + i, S);
         int X = it & 3;
         long long tm = it >> 2;
         int m = (int)(tm % S.nm), t = (int)(tm / S.nm);
@@ -527,7 +661,7 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             long long o = (long long)S.perm[k] * P.g.plane;
-            qs[k] = (fx(ld(cl + o)) + fx(ld(cr + o))) * fx(0.5);
+            qs[k] = (fx(ldc(cl + o, S)) + fx(ldc(cr + o, S))) * fx(0.5);
         }
         eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
 #pragma unroll
@@ -537,7 +671,7 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
         double v[4][2], d[4][2];
         tang_ao_x4(Lm, Rm, x, ak, gmask, v, d);
         gp_positivity(P, S, t, m, X, v, d);
-        // component q of both Gauss points (layout of store_gp)
+        // component q of both Gauss points (Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry)
         long long plane = (long long)S.nt * S.nm;
         long long o = (long long)t * S.nm + m;
         int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
@@ -546,8 +680,8 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
             if (k != q) continue;
 #pragma unroll
             for (int g = 0; g < 2; g++) {
-                S.gp[(long long)((g * 6 + qv) * 4 + k) * plane + o] = v[k][g];
-                if (X <= 1) S.gp[(long long)((g * 6 + qv + 2) * 4 + k) * plane + o] = d[k][g] * S.inv_ht;
+                stc(S.gp + (long long)((g * 6 + qv) * 4 + k) * plane + o, v[k][g], S);
+                if (X <= 1) stc(S.gp + (long long)((g * 6 + qv + 2) * 4 + k) * plane + o, d[k][g] * S.inv_ht, S);
             }
         }
     }
@@ -577,15 +711,15 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
 #pragma unroll
         for (int q = 0; q < 6; q++)
 #pragma unroll
-            for (int k = 0; k < NV; k++) Wq[q][k] = ld(S.gp + (long long)((g * 6 + q) * 4 + k) * per + o);
+            for (int k = 0; k < NV; k++) Wq[q][k] = ldc(S.gp + (long long)((g * 6 + q) * 4 + k) * per + o, S);
     } else {
         long long plane = (long long)S.nlines * S.nm;
 #pragma unroll
         for (int k = 0; k < NV; k++) {
-            Wq[0][k] = ld(S.line + (long long)(0 * NV + k) * plane + o);
-            Wq[1][k] = ld(S.line + (long long)(2 * NV + k) * plane + o);
-            Wq[3][k] = ld(S.line + (long long)(1 * NV + k) * plane + o);
-            Wq[4][k] = ld(S.line + (long long)(3 * NV + k) * plane + o);
+            Wq[0][k] = ldc(S.line + (long long)(0 * NV + k) * plane + o, S);
+            Wq[1][k] = ldc(S.line + (long long)(2 * NV + k) * plane + o, S);
+            Wq[3][k] = ldc(S.line + (long long)(1 * NV + k) * plane + o, S);
+            Wq[4][k] = ldc(S.line + (long long)(3 * NV + k) * plane + o, S);
             Wq[2][k] = 0.0; Wq[5][k] = 0.0;
         }
     }
@@ -600,8 +734,8 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         int gk = S.perm[k];
-        S.flux[(long long)((g * 2 + 0) * NV + gk) * per + o] = o0[k];
-        if (STAGE == 0) S.flux[(long long)((g * 2 + 1) * NV + gk) * per + o] = o1[k];
+        stc(S.flux + (long long)((g * 2 + 0) * NV + gk) * per + o, o0[k], S);
+        if (STAGE == 0) stc(S.flux + (long long)((g * 2 + 1) * NV + gk) * per + o, o1[k], S);
     }
 }
 
@@ -644,24 +778,24 @@ __device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const
         for (int s = 0; s < 2; s++) {
             const double* fb = Sx.flux;
             if constexpr (DIM == 2) {
-                fx0[s] = 0.5 * ld(fb + (long long)((0 * 2 + 0) * NV + k) * perx + ox + s) + 0.5 * ld(fb + (long long)((1 * 2 + 0) * NV + k) * perx + ox + s);
-                fx1[s] = STAGE == 0 ? 0.5 * ld(fb + (long long)((0 * 2 + 1) * NV + k) * perx + ox + s) + 0.5 * ld(fb + (long long)((1 * 2 + 1) * NV + k) * perx + ox + s) : 0.0;
+                fx0[s] = 0.5 * ldc(fb + (long long)((0 * 2 + 0) * NV + k) * perx + ox + s, g) + 0.5 * ldc(fb + (long long)((1 * 2 + 0) * NV + k) * perx + ox + s, g);
+                fx1[s] = STAGE == 0 ? 0.5 * ldc(fb + (long long)((0 * 2 + 1) * NV + k) * perx + ox + s, g) + 0.5 * ldc(fb + (long long)((1 * 2 + 1) * NV + k) * perx + ox + s, g) : 0.0;
                 const double* gb = Sy.flux;
-                fy0[s] = 0.5 * ld(gb + (long long)((0 * 2 + 0) * NV + k) * pery + oy + s) + 0.5 * ld(gb + (long long)((1 * 2 + 0) * NV + k) * pery + oy + s);
-                fy1[s] = STAGE == 0 ? 0.5 * ld(gb + (long long)((0 * 2 + 1) * NV + k) * pery + oy + s) + 0.5 * ld(gb + (long long)((1 * 2 + 1) * NV + k) * pery + oy + s) : 0.0;
+                fy0[s] = 0.5 * ldc(gb + (long long)((0 * 2 + 0) * NV + k) * pery + oy + s, g) + 0.5 * ldc(gb + (long long)((1 * 2 + 0) * NV + k) * pery + oy + s, g);
+                fy1[s] = STAGE == 0 ? 0.5 * ldc(gb + (long long)((0 * 2 + 1) * NV + k) * pery + oy + s, g) + 0.5 * ldc(gb + (long long)((1 * 2 + 1) * NV + k) * pery + oy + s, g) : 0.0;
             } else {
-                fx0[s] = ld(fb + (long long)(0 * NV + k) * perx + ox + s);
-                fx1[s] = STAGE == 0 ? ld(fb + (long long)(1 * NV + k) * perx + ox + s) : 0.0;
+                fx0[s] = ldc(fb + (long long)(0 * NV + k) * perx + ox + s, g);
+                fx1[s] = STAGE == 0 ? ldc(fb + (long long)(1 * NV + k) * perx + ox + s, g) : 0.0;
             }
         }
         if (STAGE == 0) {
-            double w = ld(Win + cell + (long long)k * g.plane);
+            double w = ldc(Win + cell + (long long)k * g.plane, g);
             double ws = w - (fx0[1] - fx0[0]) * inv_dx;
             double wa = w - (fx1[1] - fx1[0]) * inv_dx;
             if (DIM == 2) { ws = ws - (fy0[1] - fy0[0]) * inv_dy; wa = wa - (fy1[1] - fy1[0]) * inv_dy; }
             out[k] = ws; acc[k] = wa;
         } else {
-            double a = ld(Acc + cell + (long long)k * g.plane);
+            double a = ldc(Acc + cell + (long long)k * g.plane, g);
             double wn = a - (fx0[1] - fx0[0]) * inv_dx;
             if (DIM == 2) wn = wn - (fy0[1] - fy0[0]) * inv_dy;
             out[k] = wn;
@@ -669,8 +803,8 @@ __device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const
     }
 #pragma unroll
     for (int k = 0; k < NV; k++) {
-        Wout[cell + (long long)k * g.plane] = out[k];
-        if (STAGE == 0) Acc[cell + (long long)k * g.plane] = acc[k];
+        stc(Wout + cell + (long long)k * g.plane, out[k], g);
+        if (STAGE == 0) stc(Acc + cell + (long long)k * g.plane, acc[k], g);
     }
     // rho > 0 and p > 0, the latter as rho E - |m|^2/2 > 0 (no division)
     double ke = DIM == 2 ? 0.5 * fma(out[1], out[1], out[2] * out[2]) : 0.5 * out[1] * out[1];
@@ -835,6 +969,19 @@ cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters)
     return cudaGetLastError();
 }
 
+int debug_bounds_read(unsigned long long* count, unsigned long long* first)
+{
+#ifdef HGKS_DEBUG_BOUNDS
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_dbg_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(first, g_dbg_first, sizeof(unsigned long long));
+    return e == cudaSuccess ? 1 : -1;
+#else
+    *count = 0;
+    *first = 0;
+    return 0;
+#endif
+}
+
 int device_sm_count()
 {
     int dev = 0, n = 0;
@@ -897,11 +1044,11 @@ static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
     });
     if constexpr (DIM == 2) {
         timed(s, KC_RAWT, 1, [&] {
-            long long n = (long long)(S.nt + 2) * S.nm;
+            long long n = (long long)(S.nt + 2) * S.nm * S.tlanes;
             k_raw_tflags<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl);
         });
         timed(s, KC_TANG, 1, [&] {
-            long long n = (long long)S.nt * S.nm;
+            long long n = (long long)S.nt * S.nm * S.tlanes;
             k_tang<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl, stage);
         });
         timed(s, KC_TANG_AO, 1, [&] {
@@ -1028,8 +1175,8 @@ void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* 
                 case BK_RAWN: b = sweep_used ? blocks_for((long long)S.nlines * (S.nn + 4), t) : 0; break;
                 case BK_NORMAL: b = sweep_used ? blocks_for((long long)S.nlines * S.nm, t) : 0; break;
                 case BK_NAO: b = sweep_used ? blocks_for((long long)S.nlines * S.nm * 2 * 4, t * 8) : 0; break;
-                case BK_RAWT: b = dim == 2 ? blocks_for((long long)(S.nt + 2) * S.nm, t) : 0; break;
-                case BK_TANG: b = dim == 2 ? blocks_for((long long)S.nt * S.nm, t) : 0; break;
+                case BK_RAWT: b = dim == 2 ? blocks_for((long long)(S.nt + 2) * S.nm * S.tlanes, t) : 0; break;
+                case BK_TANG: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * S.tlanes, t) : 0; break;
                 case BK_TAO: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * 4 * 4, t * 8) : 0; break;
                 case BK_FLUX: b = sweep_used ? blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t) : 0; break;
                 case BK_UPD: b = blocks_for(cells, t); break;

@@ -14,7 +14,9 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libhgks.so")
+# HGKS_DEBUG_BOUNDS=1 in the environment loads the debug build (every kernel access range-checked)
+LIB_PATH = os.path.join(_PKG, "_lib", "libhgks_debug.so" if os.environ.get("HGKS_DEBUG_BOUNDS") == "1"
+                        else "libhgks.so")
 
 HGKS_OK = 0
 HGKS_EINVAL = -1
@@ -35,7 +37,7 @@ EXPORTED = [
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
     "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status", "hgks_batch_info",
     "hgks_batch_last_error",
-    "hgks_batch_destroy", "hgks_probe_fp64", "hgks_step_noalloc",
+    "hgks_batch_destroy", "hgks_debug_bounds", "hgks_probe_fp64", "hgks_step_noalloc",
 ]
 HGKS_BATCH_GRAPH = 1
 HGKS_BATCH_AUTOTUNE = 2
@@ -114,6 +116,7 @@ def lib():
         L.hgks_batch_destroy.argtypes = [vp]
         L.hgks_batch_destroy.restype = None
         L.hgks_probe_fp64.argtypes = [vp, dp, dp, ip]
+        L.hgks_debug_bounds.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
         L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp, vp]
         _lib = L
         return L
@@ -338,6 +341,16 @@ def run(cfg: dict, W, t_end: float, max_steps: int = 1 << 30, t0: float = 0.0):
         return s.hgks_get_state(), s.hgks_get_time(), n
     finally:
         s.hgks_destroy_solver()
+
+
+def hgks_debug_bounds():
+    """(checked, count, first_address): whether this library checks every kernel access
+    (the debug build), how many out-of-range accesses it skipped, and the first address."""
+    n, a = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    rc = lib().hgks_debug_bounds(ctypes.byref(n), ctypes.byref(a))
+    if rc < 0:
+        raise HGKSError(rc, lib().hgks_last_error(None).decode())
+    return bool(rc), n.value, a.value
 
 
 def hgks_probe_fp64(stream=None):

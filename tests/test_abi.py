@@ -82,3 +82,9 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(hgks, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         hgks.lib()
+
+
+def test_normal_build_reports_no_bounds_checks(L):
+    """hgks_debug_bounds needs no device in the normal build: it reports that the checks are
+    not compiled in (the debug build is _lib/libhgks_debug.so)."""
+    assert hgks.hgks_debug_bounds() == (False, 0, 0)
