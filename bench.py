@@ -70,12 +70,17 @@ WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS,
 #   closed-form count.)
 FLUX_ALG_FLOP_PER_GP = (1433.0 + 1389.0) / 2
 ORACLE_FLUX_FLOP_PER_GP = 7025.0
+# On large sweeps the flux kernel also reconstructs its Gauss point's smooth tangential passes
+# (the quartic of Sec. 2.3.3 at the Gauss point): 16 values and 8 tangential derivatives of 5
+# terms each (1 mul + 4 fma = 9 operations), 2 positivity tests (6) and 8 derivative scalings:
+# 236 operations per Gauss point, counted by hand from the formulas.
+FLUX_KERNEL_TANG_FLOP_PER_GP = 16 * 9 + 8 * 9 + 2 * 6 + 8
 NONFLUX_FLOP_PER_CELL_STAGE = {"linear": 2721.3, "wenoao": 19486.7, "hybrid": 3525.5,
                                "hybrid_troubled_fraction": 0.004106}
-# DRAM bytes (read + write) per flux launch, ncu at 512^2 (113.0 and 113.8 MB first stage, 106.9
-# and 107.8 MB second), scaled to 1024^2 by the Gauss points per launch (traffic is linear in
-# them: Gauss-point states in, per-Gauss-point fluxes out).
-FLUX_DRAM_BYTES_PER_GP = (113.03e6 + 113.80e6 + 106.85e6 + 107.77e6) / 4 / (2 * 512 * 513)
+# DRAM bytes (read + write) per flux launch, ncu at 512^2 (the kernel with the fused tangential
+# reconstruction, second stage: 35.23 MB read + 0.40 MB written, and 35.24 + 0.63 MB), scaled to
+# 1024^2 by the Gauss points per launch (the line buffer it reads is linear in them).
+FLUX_DRAM_BYTES_PER_GP = (35.23e6 + 0.40e6 + 35.24e6 + 0.63e6) / 2 / (2 * 512 * 513)
 
 
 def algorithmic_flop_per_cell_stage(n, troubled_fraction):
@@ -635,15 +640,19 @@ def main():
     if flux_calls:
         avg_ms = flux_ms / flux_calls
         gp_per_launch = 2 * (n + 1) * n          # Gauss points of one sweep
-        achieved = FLUX_ALG_FLOP_PER_GP * gp_per_launch / (avg_ms * 1e-3) / 1e12
+        # the kernel's work per Gauss point: the flux, and on sweeps of 65 536 segments or more the
+        # fused reconstruction of the smooth tangential passes
+        per_gp = FLUX_ALG_FLOP_PER_GP + (FLUX_KERNEL_TANG_FLOP_PER_GP if n * (n + 1) >= 65536 else 0.0)
+        achieved = per_gp * gp_per_launch / (avg_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops,
                     "traffic": FLUX_DRAM_BYTES_PER_GP * gp_per_launch if n == N_SIDE else None,
                     "kernel": "gks_flux", "avg_launch_ms": avg_ms,
-                    "flop_per_launch": FLUX_ALG_FLOP_PER_GP * gp_per_launch,
-                    "unit_of_work": "Gauss-point flux: %.0f algorithmic FP64 operations (closed form; "
-                                    "the oracle's literal moment integration takes %.0f)"
-                                    % (FLUX_ALG_FLOP_PER_GP, ORACLE_FLUX_FLOP_PER_GP),
+                    "flop_per_launch": per_gp * gp_per_launch,
+                    "unit_of_work": "Gauss point: %.0f algorithmic FP64 operations = flux %.0f (closed form; the "
+                                    "oracle's literal moment integration takes %.0f) + reconstruction of the smooth "
+                                    "tangential passes %.0f" % (per_gp, FLUX_ALG_FLOP_PER_GP, ORACLE_FLUX_FLOP_PER_GP,
+                                                                 per_gp - FLUX_ALG_FLOP_PER_GP),
                     "peak_note": "derived: %d SMs (device attribute) x 4 FP64 flop/clk/SM x %s MHz (median SM "
                                  "clock of the timed region); the DFMA-chain probe hgks_probe_fp64 gives %.3f "
                                  "TFLOP/s at %s MHz (%.2f flop/clk/SM)"

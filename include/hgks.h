@@ -188,6 +188,18 @@ typedef struct hgks_batch hgks_batch;
  * filling one GPU with many small solves.  Errors: HGKS_EINVAL, HGKS_ENOMEM, HGKS_ECUDA. */
 int hgks_batch_create(hgks_solver* const* solvers, int n, void* stream, hgks_batch** out);
 
+/* Replace the batch's solvers by solvers[0..n) (n >= 1, the batch's dimension and
+ * device), keeping its stream and the block sizes chosen by the autotuner: for a
+ * scheduler whose set of resident solves changes between groups of steps.  Waits
+ * for the batch's stream and the new solvers' streams; the device arrays are
+ * reused while n fits the largest membership so far (grown by doubling
+ * otherwise); a captured graph is re-captured at the next graph step and the
+ * executable graph updated in place (the kernel sequence is the same) instead of
+ * re-instantiated.  The end times start at 0: pass t_end to the next
+ * hgks_batch_step.  Results stay bit-identical to stepping each solver alone.
+ * Errors: HGKS_EINVAL, HGKS_ENOMEM, HGKS_ECUDA (message in hgks_batch_last_error(b)). */
+int hgks_batch_update(hgks_batch* b, hgks_solver* const* solvers, int n);
+
 /* Enqueue nsteps batched S2O4 steps.  t_end (length n, may be NULL to keep the
  * previous values; initially 0) is each solver's end time with hgks_step's
  * clipping rule; solvers at their end time or with a latched error are left

@@ -92,7 +92,7 @@ int validate(const hgks_config* c, char* err)
 
 struct Layout {
     size_t total;
-    size_t off_W, off_Ws, off_Acc, off_ctrl, off_line, off_gp;
+    size_t off_W, off_Ws, off_Acc, off_ctrl, off_desc, off_line, off_gp;
     size_t off_rawN[2], off_flagN[2], off_rawT[2], off_flagT[2], off_itemsN[2], off_itemsT[2], off_flux[2];
 };
 
@@ -166,6 +166,7 @@ Layout plan(const hgks_config* c, const Params& P, const Sweep* sw)
     size_t st = (size_t)P.g.nv * P.g.plane * sizeof(double);
     L.off_W = take(st); L.off_Ws = take(st); L.off_Acc = take(st);
     L.off_ctrl = take(sizeof(Ctrl));
+    L.off_desc = take(sizeof(SolveDesc));
     int nd = c->dim;
     size_t maxline = 0, maxgp = 0;
     for (int d = 0; d < nd; d++) {
@@ -290,7 +291,11 @@ extern "C" int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_sol
     s->timing = 0;
     s->timer_ms.assign(KC_COUNT, 0.0);
     s->timer_calls.assign(KC_COUNT, 0);
+    s->d_self = (SolveDesc*)(base + L.off_desc);
+    SolveDesc self;
+    batch_fill_desc(s, self);
     e = cudaMemsetAsync(s->pool, 0, L.total, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_self, &self, sizeof(SolveDesc), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = launch_set_time(s, 0.0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -488,6 +493,8 @@ struct hgks_batch {
     cudaEvent_t done_ev = nullptr;      // the batch stream after the last enqueued step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int graph_stale = 0;                // the plan changed since the capture: recapture, update exec
+    int cap = 0;                        // solvers the device arrays hold
     long long steps_enqueued = 0;
     char err[512];
 };
@@ -504,9 +511,59 @@ int batch_upload_plan(hgks_batch* b, const int* tpb)
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) { set_err(b->err, "plan upload failed: %s", cudaGetErrorString(e)); return HGKS_ECUDA; }
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (b->exec) b->graph_stale = 1;    // the next graph step recaptures and updates the executable graph
     return HGKS_OK;
+}
+
+// (Re)build the per-stream ordering events for the solvers' own streams.
+int batch_set_streams(hgks_batch* b)
+{
+    for (cudaEvent_t ev : b->other_ev) cudaEventDestroy(ev);
+    b->others.clear();
+    b->other_ev.clear();
+    for (int i = 0; i < b->n; i++) {
+        cudaStream_t st = b->solvers[i]->stream;
+        bool seen = st == b->stream;
+        for (cudaStream_t o : b->others) seen = seen || o == st;
+        if (seen) continue;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) { set_err(b->err, "event creation failed: %s", cudaGetErrorString(e)); return HGKS_ECUDA; }
+        b->others.push_back(st);
+        b->other_ev.push_back(ev);
+    }
+    return HGKS_OK;
+}
+
+// Device arrays for at least n solvers (grown by doubling; contents not kept).
+int batch_reserve(hgks_batch* b, int n)
+{
+    if (n <= b->cap) return HGKS_OK;
+    int cap = b->cap * 2 > n ? b->cap * 2 : n;
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_boff) cudaFree(b->d_boff);
+    if (b->d_tend) cudaFree(b->d_tend);
+    if (b->h_tend) cudaFreeHost(b->h_tend);
+    b->d_desc = nullptr; b->d_boff = nullptr; b->d_tend = nullptr; b->h_tend = nullptr; b->cap = 0;
+    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(SolveDesc) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_boff, sizeof(int) * (size_t)BK_COUNT * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tend, sizeof(double) * cap);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tend, sizeof(double) * cap);
+    if (e != cudaSuccess) { set_err(b->err, "batch allocation failed: %s", cudaGetErrorString(e)); return HGKS_ENOMEM; }
+    b->cap = cap;
+    return HGKS_OK;
+}
+
+// Upload the descriptors of the current solvers, zero end times and the plan with block sizes tpb.
+int batch_upload_members(hgks_batch* b, const int* tpb)
+{
+    std::vector<SolveDesc> h(b->n);
+    for (int i = 0; i < b->n; i++) { batch_fill_desc(b->solvers[i], h[i]); b->h_tend[i] = 0.0; }
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(SolveDesc) * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tend, b->h_tend, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->tend_ev, b->stream);
+    if (e != cudaSuccess) { set_err(b->err, "batch upload failed: %s", cudaGetErrorString(e)); return HGKS_ECUDA; }
+    return batch_upload_plan(b, tpb);
 }
 
 }  // namespace
@@ -530,36 +587,41 @@ extern "C" int hgks_batch_create(hgks_solver* const* solvers, int n, void* strea
     b->solvers.assign(solvers, solvers + n);
     b->err[0] = 0;
     for (int i = 0; i < n; i++) cudaStreamSynchronize(solvers[i]->stream);
-    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(SolveDesc) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_boff, sizeof(int) * (size_t)BK_COUNT * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tend, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tend, sizeof(double) * n);
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 * BK_COUNT && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tend_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming);
-    for (int i = 0; i < n && e == cudaSuccess; i++) {
-        cudaStream_t st = solvers[i]->stream;
-        bool seen = st == b->stream;
-        for (cudaStream_t o : b->others) seen = seen || o == st;
-        if (seen) continue;
-        cudaEvent_t ev = nullptr;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) { b->others.push_back(st); b->other_ev.push_back(ev); }
-    }
     if (e != cudaSuccess) {
-        set_err(g_create_err, "batch allocation failed: %s", cudaGetErrorString(e));
+        set_err(g_create_err, "batch event creation failed: %s", cudaGetErrorString(e));
         hgks_batch_destroy(b);
-        return HGKS_ENOMEM;
+        return HGKS_ECUDA;
     }
-    std::vector<SolveDesc> h(n);
-    for (int i = 0; i < n; i++) { batch_fill_desc(solvers[i], h[i]); b->h_tend[i] = 0.0; }
-    e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(SolveDesc) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tend, b->h_tend, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) { set_err(g_create_err, "batch upload failed: %s", cudaGetErrorString(e)); hgks_batch_destroy(b); return HGKS_ECUDA; }
-    int st = batch_upload_plan(b, kBatchTpbDefault);
+    int st = batch_reserve(b, n);
+    if (st == HGKS_OK) st = batch_set_streams(b);
+    if (st == HGKS_OK) st = batch_upload_members(b, kBatchTpbDefault);
     if (st != HGKS_OK) { set_err(g_create_err, "%s", b->err); hgks_batch_destroy(b); return st; }
     *out = b;
     return HGKS_OK;
+}
+
+extern "C" int hgks_batch_update(hgks_batch* b, hgks_solver* const* solvers, int n)
+{
+    if (!b || n < 1 || !solvers) { if (b) set_err(b->err, "need at least one solver"); return HGKS_EINVAL; }
+    for (int i = 0; i < n; i++) {
+        if (!solvers[i]) { set_err(b->err, "solver %d is NULL", i); return HGKS_EINVAL; }
+        if (solvers[i]->cfg.dim != b->dim) { set_err(b->err, "all solvers of a batch must have the same dimension"); return HGKS_EINVAL; }
+        if (solvers[i]->device != b->device) { set_err(b->err, "solver %d lives on another device", i); return HGKS_EINVAL; }
+    }
+    // the batch's earlier steps read the old descriptors: let them finish first
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n; i++) CUDA_TRY(b, cudaStreamSynchronize(solvers[i]->stream));
+    int st = batch_reserve(b, n);
+    if (st != HGKS_OK) return st;
+    b->n = n;
+    b->solvers.assign(solvers, solvers + n);
+    st = batch_set_streams(b);
+    if (st != HGKS_OK) return st;
+    return batch_upload_members(b, b->plan.tpb);
 }
 
 extern "C" void hgks_batch_destroy(hgks_batch* b)
@@ -640,15 +702,31 @@ extern "C" int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, i
     const bool use_graph = (flags & HGKS_BATCH_GRAPH) && b->stream != nullptr;
     for (int k = 0; k < left; k++) {
         if (use_graph) {
-            if (!b->exec) {
+            if (!b->exec || b->graph_stale) {
+                cudaGraph_t g = nullptr;
                 CUDA_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t e = batch_enqueue_step(b->plan, b->d_desc, b->d_boff, b->d_tend, b->stream, nullptr);
-                cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
                 if (e != cudaSuccess || e2 != cudaSuccess) {
                     set_err(b->err, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
                     return HGKS_ECUDA;
                 }
-                CUDA_TRY(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+                // the same kernels in the same order with new grids and arguments: update the
+                // executable graph in place when the driver accepts it, else instantiate anew
+                bool updated = false;
+                if (b->exec) {
+                    cudaGraphExecUpdateResultInfo info;
+                    updated = cudaGraphExecUpdate(b->exec, g, &info) == cudaSuccess;
+                    if (!updated) {
+                        (void)cudaGetLastError();
+                        cudaGraphExecDestroy(b->exec);
+                        b->exec = nullptr;
+                    }
+                }
+                if (b->graph) cudaGraphDestroy(b->graph);
+                b->graph = g;
+                b->graph_stale = 0;
+                if (!updated) CUDA_TRY(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
             }
             CUDA_TRY(b, cudaGraphLaunch(b->exec, b->stream));
         } else {
@@ -841,8 +919,12 @@ extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, dou
         S.hi = b + L.total;
     }
     const GridGeom& g = s.P.g;
+    s.d_self = (SolveDesc*)(b + L.off_desc);
+    SolveDesc self;
+    batch_fill_desc(&s, self);
     // the array keeps the previous call's contents: start every call from zero
     e = cudaMemsetAsync(base, 0, L.total, s.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_self, &self, sizeof(SolveDesc), cudaMemcpyHostToDevice, s.stream);
     for (int k = 0; k < g.nv && e == cudaSuccess; k++)
         e = cudaMemcpy2DAsync(s.W + g.origin + (long long)k * g.plane, (size_t)g.pitch * sizeof(double),
                               W_in + (size_t)k * g.nx * g.ny, (size_t)g.nx * sizeof(double),

@@ -117,6 +117,7 @@ struct hgks_solver {
     double* Acc;     // padded accumulator of stage 1
     hgks::Ctrl* ctrl;        // device
     hgks::Ctrl* ctrl_host;   // pinned mirror
+    hgks::SolveDesc* d_self; // device copy of this solver's descriptor (the kernels shared with batches read it)
     void* pool;              // single device allocation holding all buffers
     size_t pool_bytes;
     uint8_t* cap[2][2][2];   // captured flags [stage][sweep][kind]

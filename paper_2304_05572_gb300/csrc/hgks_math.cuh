@@ -435,7 +435,7 @@ __device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4],
     }
     fx u[5];
 #pragma unroll
-    for (int s = 0; s < 5; s++) u[s] = ((Lq[0] * x[s][0] + Lq[1] * x[s][1]) + Lq[2] * x[s][2]) + Lq[3] * x[s][3];
+    for (int s = 0; s < 5; s++) u[s] = xfma(Lq[3], x[s][3], xfma(Lq[2], x[s][2], xfma(Lq[1], x[s][1], Lq[0] * x[s][0])));
     double cvq[2], cdq[2];
     gauss_ao(u, ak, cvq, cdq);
     double cv[4][2], cd[4][2];
@@ -544,7 +544,7 @@ HGKS_HD __forceinline__ void jac_x(const MState<DIM>& s, const double* d, const 
     if constexpr (DIM == 2) {
         const double hq = 0.5 * fma(s.U, s.U, s.V * s.V);
         const double dp = gm1 * fma(hq, d[0], fma(-s.U, d[1], fma(-s.V, d[2], d[3])));
-        const double dU = (d[1] - s.U * d[0]) * s.ri;
+        const double dU = fma(-s.U, d[0], d[1]) * s.ri;
         out[0] = d[1];
         out[1] = fma(s.U, fma(-s.U, d[0], 2.0 * d[1]), dp);
         out[2] = fma(s.V, d[1], s.U * fma(-s.V, d[0], d[2]));
@@ -552,7 +552,7 @@ HGKS_HD __forceinline__ void jac_x(const MState<DIM>& s, const double* d, const 
     } else {
         const double hq = 0.5 * s.U * s.U;
         const double dp = gm1 * fma(hq, d[0], fma(-s.U, d[1], d[2]));
-        const double dU = (d[1] - s.U * d[0]) * s.ri;
+        const double dU = fma(-s.U, d[0], d[1]) * s.ri;
         out[0] = d[1];
         out[1] = fma(s.U, fma(-s.U, d[0], 2.0 * d[1]), dp);
         out[2] = fma(dU, g, s.U * (d[2] + dp));
@@ -564,7 +564,7 @@ HGKS_HD __forceinline__ void jac_y(const MState<2>& s, const double* e, const do
     const double g = s.E + s.p;
     const double hq = 0.5 * fma(s.U, s.U, s.V * s.V);
     const double dp = gm1 * fma(hq, e[0], fma(-s.U, e[1], fma(-s.V, e[2], e[3])));
-    const double dV = (e[2] - s.V * e[0]) * s.ri;
+    const double dV = fma(-s.V, e[0], e[2]) * s.ri;
     out[0] = e[2];
     out[1] = fma(s.U, e[2], s.V * fma(-s.U, e[0], e[1]));
     out[2] = fma(s.V, fma(-s.V, e[0], 2.0 * e[2]), dp);
@@ -600,28 +600,28 @@ HGKS_HD __forceinline__ void pi_sigma_dir(const MState<DIM>& s, const double* d,
     const double U2 = U * U;
     if constexpr (DIM == 2) {
         const double V2 = V * V;
-        const double hq = 0.5 * (U2 + V2);
+        const double hq = 0.5 * fma(U, U, V2);
         // Pi along d
-        double dU = (d[1] - U * d[0]) * s.ri, dV = (d[2] - V * d[0]) * s.ri;
+        double dU = fma(-U, d[0], d[1]) * s.ri, dV = fma(-V, d[0], d[2]) * s.ri;
         double dp = gm1 * fma(hq, d[0], fma(-U, d[1], fma(-V, d[2], d[3])));
-        double dh = (dp - h * d[0]) * s.ri;
-        const double u2 = U2 + h, v2 = V2 + h;
-        const double p0 = u2, p1 = U * (U2 + 3.0 * h), p2 = u2 * V;
-        const double p3 = 0.5 * (fma(U2, U2 + 6.0 * h, 3.0 * h * h) + u2 * v2 + u2 * K * h);
-        const double p3U = U * (2.0 * U2 + 6.0 * h + v2 + K * h);
-        const double p3h = 0.5 * (7.0 * U2 + V2 + 8.0 * h + K * (U2 + 2.0 * h));
+        double dh = fma(-h, d[0], dp) * s.ri;
+        const double u2 = fma(U, U, h), v2 = fma(V, V, h);
+        const double p0 = u2, p1 = U * fma(3.0, h, U2), p2 = u2 * V;
+        const double p3 = 0.5 * fma(u2 * K, h, fma(u2, v2, fma(U2, fma(6.0, h, U2), 3.0 * h * h)));
+        const double p3U = U * fma(K, h, fma(6.0, h, 2.0 * U2) + v2);
+        const double p3h = 0.5 * fma(K, fma(2.0, h, U2), fma(8.0, h, fma(7.0, U2, V2)));
         out[0] = fma(p0, d[0], r * fma(2.0 * U, dU, dh));
         out[1] = fma(p1, d[0], r * fma(3.0 * u2, dU, 3.0 * U * dh));
         out[2] = fma(p2, d[0], r * fma(2.0 * U * V, dU, fma(u2, dV, V * dh)));
         out[3] = fma(p3, d[0], r * fma(p3U, dU, fma(u2 * V, dV, p3h * dh)));
         // Sigma along e
-        dU = (e[1] - U * e[0]) * s.ri; dV = (e[2] - V * e[0]) * s.ri;
+        dU = fma(-U, e[0], e[1]) * s.ri; dV = fma(-V, e[0], e[2]) * s.ri;
         dp = gm1 * fma(hq, e[0], fma(-U, e[1], fma(-V, e[2], e[3])));
-        dh = (dp - h * e[0]) * s.ri;
+        dh = fma(-h, e[0], dp) * s.ri;
         const double UV = U * V, k6 = 6.0 + K;
-        const double s0 = UV, s1 = u2 * V, s2 = U * v2, s3 = 0.5 * UV * (U2 + V2 + k6 * h);
-        const double s3U = 0.5 * V * (3.0 * U2 + V2 + k6 * h);
-        const double s3V = 0.5 * U * (U2 + 3.0 * V2 + k6 * h);
+        const double s0 = UV, s1 = u2 * V, s2 = U * v2, s3 = 0.5 * UV * fma(k6, h, fma(U, U, V2));
+        const double s3U = 0.5 * V * fma(k6, h, fma(3.0, U2, V2));
+        const double s3V = 0.5 * U * fma(k6, h, fma(3.0, V2, U2));
         const double s3h = 0.5 * k6 * UV;
         out[0] += fma(s0, e[0], r * fma(V, dU, U * dV));
         out[1] += fma(s1, e[0], r * fma(2.0 * UV, dU, fma(u2, dV, V * dh)));
@@ -630,14 +630,14 @@ HGKS_HD __forceinline__ void pi_sigma_dir(const MState<DIM>& s, const double* d,
     } else {
         (void)e;
         const double hq = 0.5 * U2;
-        const double dU = (d[1] - U * d[0]) * s.ri;
+        const double dU = fma(-U, d[0], d[1]) * s.ri;
         const double dp = gm1 * fma(hq, d[0], fma(-U, d[1], d[2]));
-        const double dh = (dp - h * d[0]) * s.ri;
-        const double u2 = U2 + h;
-        const double p0 = u2, p1 = U * (U2 + 3.0 * h);
-        const double p2 = 0.5 * (fma(U2, U2 + 6.0 * h, 3.0 * h * h) + u2 * K * h);
-        const double p2U = U * (2.0 * U2 + 6.0 * h + K * h);
-        const double p2h = 0.5 * (6.0 * U2 + 6.0 * h + K * (U2 + 2.0 * h));
+        const double dh = fma(-h, d[0], dp) * s.ri;
+        const double u2 = fma(U, U, h);
+        const double p0 = u2, p1 = U * fma(3.0, h, U2);
+        const double p2 = 0.5 * fma(u2 * K, h, fma(U2, fma(6.0, h, U2), 3.0 * h * h));
+        const double p2U = U * fma(K, h, fma(6.0, h, 2.0 * U2));
+        const double p2h = 0.5 * fma(K, fma(2.0, h, U2), fma(6.0, h, 6.0 * U2));
         out[0] = fma(p0, d[0], r * fma(2.0 * U, dU, dh));
         out[1] = fma(p1, d[0], r * fma(3.0 * u2, dU, 3.0 * U * dh));
         out[2] = fma(p2, d[0], r * fma(p2U, dU, p2h * dh));
@@ -897,7 +897,7 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     double tau;
     if (fc.tau_zero) tau = 0.0;
     else if (fc.viscous) tau = fma(fc.c2 * jump, dt, fc.mu / sc.p);
-    else tau = (fc.c1 + fc.c2 * jump) * dt;
+    else tau = fma(fc.c2, jump, fc.c1) * dt;
 
     // time integrals of the factors of Eq. (10) over [0, d], d = dt and dt/2
     double Cd[6], Ch[6];
@@ -925,7 +925,7 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     double A0[6], A1[6];
 #pragma unroll
     for (int j = 0; j < 6; j++) {
-        if constexpr (STAGE == 0) { A0[j] = Ch[j]; A1[j] = (8.0 * Ch[j] - Cd[j]) * (1.0 / 3.0); }
+        if constexpr (STAGE == 0) { A0[j] = Ch[j]; A1[j] = fma(8.0, Ch[j], -Cd[j]) * (1.0 / 3.0); }
         else                      { A0[j] = (4.0 / 3.0) * fma(-2.0, Ch[j], Cd[j]); A1[j] = 0.0; }
     }
 

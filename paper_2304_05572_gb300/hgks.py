@@ -35,7 +35,8 @@ EXPORTED = [
     "hgks_config_default", "hgks_create_solver", "hgks_destroy_solver", "hgks_set_state", "hgks_step",
     "hgks_get_state", "hgks_get_time", "hgks_get_stats", "hgks_set_flag_capture", "hgks_flags_size",
     "hgks_get_flags", "hgks_set_timing", "hgks_get_timing", "hgks_last_error", "hgks_footprint_bytes",
-    "hgks_batch_create", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status", "hgks_batch_info",
+    "hgks_batch_create", "hgks_batch_update", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status",
+    "hgks_batch_info",
     "hgks_batch_last_error",
     "hgks_batch_destroy", "hgks_debug_bounds", "hgks_probe_fp64", "hgks_step_noalloc",
 ]
@@ -107,6 +108,7 @@ def lib():
         L.hgks_footprint_bytes.argtypes = [ctypes.POINTER(hgks_config)]
         L.hgks_footprint_bytes.restype = ctypes.c_size_t
         L.hgks_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.hgks_batch_update.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int]
         L.hgks_batch_step.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int]
         L.hgks_batch_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.hgks_batch_status.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
@@ -291,6 +293,13 @@ class Batch:
     def _check(self, rc):
         if rc != HGKS_OK:
             raise HGKSError(rc, lib().hgks_batch_last_error(self._h).decode())
+
+    def hgks_batch_update(self, solvers):
+        """Replace the batch's solvers (hgks_batch_update); the same stream and block sizes."""
+        new = list(solvers)
+        arr = (ctypes.c_void_p * len(new))(*[sv.handle for sv in new])
+        self._check(lib().hgks_batch_update(self._h, arr, len(new)))
+        self.solvers = new
 
     def hgks_batch_step(self, t_end=None, nsteps=1, graph=True, autotune=False):
         te = None

@@ -63,13 +63,17 @@ class GpuBackend:
         return s
 
     def _batch(self, dim, handles):
+        """The dimension's batch over exactly these solvers: created once, then updated in place
+        when the resident set changes (no reallocation, graph updated rather than rebuilt)."""
         key = tuple(handles)
         cur = self._batches.get(dim)
         if cur is not None and cur[0] == key:
             return cur[1]
         if cur is not None:
-            cur[1].hgks_batch_destroy()
-        b = hgks.Batch(list(key), stream=self.streams[dim])
+            b = cur[1]
+            b.hgks_batch_update(list(key))
+        else:
+            b = hgks.Batch(list(key), stream=self.streams[dim])
         self._batches[dim] = (key, b)
         return b
 

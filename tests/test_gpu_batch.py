@@ -173,3 +173,36 @@ def test_batch_mixes_prandtl_fixed_and_bgk_solvers():
         assert np.array_equal(s.hgks_get_state(), ref)
         assert s.hgks_get_time() == t_ref
     b.hgks_batch_destroy()
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_update_changes_members_and_keeps_bits(graph):
+    """hgks_batch_update: a batch of A and B takes 3 steps, is updated in place to B, C, D
+    (more members than before: the device arrays grow) and takes 4 more, then to D alone
+    (fewer: arrays reused) and takes 2 more.  Every solver's state equals its solo run with
+    the same number of steps, with and without the (updated) CUDA graph."""
+    import torch
+    cases = _cases_2d()[:4]
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cfg, W in cases:
+        s = hgks.Solver(cfg, stream=stream)
+        s.hgks_set_state(np.ascontiguousarray(W))
+        solvers.append(s)
+    A, B, C, D = solvers
+    b = hgks.Batch([A, B], stream=stream)
+    b.hgks_batch_step([1.0, 1.0], nsteps=3, graph=graph)
+    b.hgks_batch_sync()
+    b.hgks_batch_update([B, C, D])
+    b.hgks_batch_step([1.0, 1.0, 1.0], nsteps=4, graph=graph)
+    b.hgks_batch_sync()
+    b.hgks_batch_update([D])
+    b.hgks_batch_step([1.0], nsteps=2, graph=graph)
+    b.hgks_batch_sync()
+    b.hgks_batch_destroy()
+    for (cfg, W), s, n in zip(cases, solvers, (3, 7, 4, 6)):
+        ref, _, n_ref = _alone(cfg, W, 1.0, n)
+        assert int(s.hgks_get_stats()["steps"]) == n_ref == n
+        assert np.array_equal(s.hgks_get_state(), ref)
+    for s in solvers:
+        s.hgks_destroy_solver()
