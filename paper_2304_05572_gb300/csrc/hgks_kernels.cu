@@ -371,49 +371,87 @@ __global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* 
 }
 
 
-// One troubled side per aligned group of 4 lanes (weno_ao_face_x4: lane q carries characteristic
-// field q); `start`, `stride` count lane groups.  Lane r stores component r.
+// Troubled items of one compacted WENO-AO pass at or above which every item gets one lane, below
+// which an aligned group of 4 lanes (one characteristic field per lane).  The lane-group form
+// repeats the eigenvector work in each of its lanes (about 1.9 times the FP64 instructions per
+// item) and pays only while the items leave the schedulers short of warps: below ~10^4 items the
+// one-lane chain of a few thousand FP64 instructions sets the pass's duration, above it the
+// one-lane form's lower instruction count does.  A constant, not a function of the launch, so
+// that a solve takes the same form in its own kernels and in batched ones.
+constexpr unsigned int kAoOneLaneMin = 8192;
+
+// The window (cells i-2..i+2 across the face, all components) and the face average of the
+// troubled side `it` of the normal pass.
 template <int NV>
-__device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
+__device__ __forceinline__ void normal_ao_item(const Params& P, const Sweep& S, const double* __restrict__ W, uint32_t it,
+                                               double (*Qw)[NV], double* Qs, int& side, int& L, int& m)
+{
+    side = it & 1;
+    const long long lm = it >> 1;
+    m = (int)(lm % S.nm); L = (int)(lm / S.nm);
+    const int t = L + S.tlo;
+    const int c = m - 1 + side;
+    const double* base = cellp(P, S, W, t, c - 2);
+#pragma unroll
+    for (int s = 0; s < 5; s++)
+#pragma unroll
+        for (int k = 0; k < NV; k++) Qw[s][k] = ldc(base + (long long)s * S.sN + (long long)S.perm[k] * P.g.plane, S);
+    const double* cl = cellp(P, S, W, t, m - 1);
+    const double* cr = cellp(P, S, W, t, m);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        long long o = (long long)S.perm[k] * P.g.plane;
+        Qs[k] = ((ex(ldc(cl + o, S)) + ex(ldc(cr + o, S))) * ex(0.5)).v;
+    }
+}
+
+// The troubled sides of the normal pass: one per lane (weno_ao_face) from kAoOneLaneMin items
+// on, else one per aligned group of 4 lanes (weno_ao_face_x4: lane q carries characteristic
+// field q and stores component q).  Both forms give the same bits.  `lane`, `lanes`: this
+// thread's index among, and the number of, the lanes working on the pass.
+template <int NV>
+__device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long lane, long long lanes)
 {
     if (ctrl->done) return;
     unsigned int n = ctrl->cnt[S.dir][0];
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
+    const long long plane = (long long)S.nlines * S.nm;
+    if (n >= kAoOneLaneMin) {
+        for (unsigned int i = (unsigned int)lane; i < n; i += (unsigned int)lanes) {
+            double Qw[5][NV], Qs[NV], val[NV], d[NV];
+            int side, L, m;
+            normal_ao_item<NV>(P, S, W, rdc(S.itemsN + i, S), Qw, Qs, side, L, m);
+            weno_ao_face<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, val, d);
+            const bool bad = nonphysical<NV>(P.gamma, val);
+            const long long o = (long long)L * S.nm + m;
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                stc(S.line + (long long)(side * NV + k) * plane + o, bad ? Qw[2][k] : val[k], S);
+                stc(S.line + (long long)((2 + side) * NV + k) * plane + o, bad ? 0.0 : (ex(d[k]) * ex(S.inv_hn)).v, S);
+            }
+        }
+        return;
+    }
     const int q = threadIdx.x & 3;
     const unsigned gmask = 0xFu << (threadIdx.x & 28);
-    for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
-        uint32_t it = rdc(S.itemsN + i, S);
-        int side = it & 1;
-        long long lm = it >> 1;
-        int m = (int)(lm % S.nm), L = (int)(lm / S.nm);
-        int t = L + S.tlo;
-        int c = m - 1 + side;
-        double Qw[5][NV], Qs[NV], val[NV], d[NV];
-        const double* base = cellp(P, S, W, t, c - 2);
-#pragma unroll
-        for (int s = 0; s < 5; s++)
-#pragma unroll
-            for (int k = 0; k < NV; k++) Qw[s][k] = ldc(base + (long long)s * S.sN + (long long)S.perm[k] * P.g.plane, S);
-        const double* cl = cellp(P, S, W, t, m - 1);
-        const double* cr = cellp(P, S, W, t, m);
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            long long o = (long long)S.perm[k] * P.g.plane;
-            Qs[k] = ((ex(ldc(cl + o, S)) + ex(ldc(cr + o, S))) * ex(0.5)).v;
-        }
-        weno_ao_face_x4<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, gmask, val, d);
-        double vq = 0.0, dq = 0.0;
+    for (unsigned int i = (unsigned int)(lane >> 2); i < n; i += (unsigned int)(lanes >> 2)) {
+        double Qw[5][NV], Qs[NV], val[NV], dq;
+        int side, L, m;
+        normal_ao_item<NV>(P, S, W, rdc(S.itemsN + i, S), Qw, Qs, side, L, m);
+        weno_ao_face_x4<NV>(P.gamma, ak, Qw, Qs, side == 0 ? +1 : -1, gmask, val, dq);
+        double vq = 0.0;
         if (nonphysical<NV>(P.gamma, val)) {
             vq = Qw[2][q < NV ? q : 0];
+            dq = 0.0;
         } else {
 #pragma unroll
             for (int k = 0; k < NV; k++)
-                if (k == q) { vq = val[k]; dq = (ex(d[k]) * ex(S.inv_hn)).v; }
+                if (k == q) vq = val[k];
+            dq = (ex(dq) * ex(S.inv_hn)).v;
         }
         if (q < NV) {
-            long long plane = (long long)S.nlines * S.nm;
             long long o = (long long)L * S.nm + m;
             stc(S.line + (long long)(side * NV + q) * plane + o, vq, S);
             stc(S.line + (long long)((2 + side) * NV + q) * plane + o, dq, S);
@@ -424,8 +462,7 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
 template <int NV>
 __global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
 {
-    b_normal_ao<NV>(P, S, W, ctrl, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2,
-                    ((long long)gridDim.x * blockDim.x) >> 2);
+    b_normal_ao<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 
@@ -645,51 +682,88 @@ __global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
 }
 
 
-// One troubled tangential pass per aligned group of 4 lanes (tang_ao_x4); `start`, `stride` count
-// lane groups.  Lane r stores component r of both Gauss points.
-__device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long start, long long stride)
+// The troubled tangential pass `it`: its pass X, segment (t, m), the eigenvectors at the face
+// average (tangential direction) and the pass's 5 line values.
+__device__ __forceinline__ void tang_ao_item(const Params& P, const Sweep& S, const double* __restrict__ W, uint32_t it,
+                                             int& X, int& t, int& m, fx (*Lm)[4], fx (*Rm)[4], fx (*x)[4])
+{
+    X = it & 3;
+    const long long tm = it >> 2;
+    m = (int)(tm % S.nm); t = (int)(tm / S.nm);
+    fx qs[4];
+    const double* cl = cellp(P, S, W, t, m - 1);
+    const double* cr = cellp(P, S, W, t, m);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        long long o = (long long)S.perm[k] * P.g.plane;
+        qs[k] = (fx(ldc(cl + o, S)) + fx(ldc(cr + o, S))) * fx(0.5);
+    }
+    eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
+#pragma unroll
+    for (int s = 0; s < 5; s++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) x[s][k] = fx(lineval(S, X, k, t - 2 + s, m));
+}
+
+// The troubled tangential passes: one per lane (tang_ao) from kAoOneLaneMin items on, else one
+// per aligned group of 4 lanes (tang_ao_x4, lane q computes and stores component q).  Free-order
+// arithmetic (the outputs only feed the flux).  `lane`, `lanes`: this thread's index among, and
+// the number of, the lanes working on the pass.
+__device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long lane, long long lanes)
 {
     if (ctrl->done) return;
     unsigned int n = ctrl->cnt[S.dir][1];
     AOConst ak;
     for (int j = 0; j < 4; j++) ak.g[j] = P.g_ao[j];
     ak.g3inv = P.g3inv; ak.gr[0] = P.gr[0]; ak.gr[1] = P.gr[1]; ak.gr[2] = P.gr[2]; ak.eps = P.eps;
-    const int q = threadIdx.x & 3;
-    const unsigned gmask = 0xFu << (threadIdx.x & 28);
-    for (unsigned int i = (unsigned int)start; i < n; i += (unsigned int)stride) {
-        uint32_t it = rdc(S.itemsT + i, S);
-        int X = it & 3;
-        long long tm = it >> 2;
-        int m = (int)(tm % S.nm), t = (int)(tm / S.nm);
-        // tangential outputs feed only the flux: free-order arithmetic (fx), FMA contraction allowed
-        fx qs[4], Lm[4][4], Rm[4][4], x[5][4];
-        const double* cl = cellp(P, S, W, t, m - 1);
-        const double* cr = cellp(P, S, W, t, m);
+    // Gauss-point buffer: Q index 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry; pass X writes its values
+    // to qv and (X = 0, 1) its tangential derivatives to qv + 2
+    const long long plane = (long long)S.nt * S.nm;
+    if (n >= kAoOneLaneMin) {
+        for (unsigned int i = (unsigned int)lane; i < n; i += (unsigned int)lanes) {
+            int X, t, m;
+            fx Lm[4][4], Rm[4][4], x[5][4];
+            tang_ao_item(P, S, W, rdc(S.itemsT + i, S), X, t, m, Lm, Rm, x);
+            double v[4][2], d[4][2];
+            tang_ao(Lm, Rm, x, ak, v, d);
+            gp_positivity(P, S, t, m, X, v, d);
+            const long long o = (long long)t * S.nm + m;
+            const int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            long long o = (long long)S.perm[k] * P.g.plane;
-            qs[k] = (fx(ldc(cl + o, S)) + fx(ldc(cr + o, S))) * fx(0.5);
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    stc(S.gp + (long long)((g * 6 + qv) * 4 + k) * plane + o, v[k][g], S);
+                    if (X <= 1) stc(S.gp + (long long)((g * 6 + qv + 2) * 4 + k) * plane + o, d[k][g] * S.inv_ht, S);
+                }
         }
-        eigvec<4>(P.gamma, qs, 0.0, 1.0, Lm, Rm);
-#pragma unroll
-        for (int s = 0; s < 5; s++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) x[s][k] = fx(lineval(S, X, k, t - 2 + s, m));
-        double v[4][2], d[4][2];
-        tang_ao_x4(Lm, Rm, x, ak, gmask, v, d);
-        gp_positivity(P, S, t, m, X, v, d);
-        // component q of both Gauss points (Q index: 0 Wl, 1 Wlx, 2 Wly, 3 Wr, 4 Wrx, 5 Wry)
-        long long plane = (long long)S.nt * S.nm;
-        long long o = (long long)t * S.nm + m;
-        int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k != q) continue;
+        return;
+    }
+    const int q = threadIdx.x & 3;
+    const int lane0 = threadIdx.x & 28;
+    const unsigned gmask = 0xFu << lane0;
+    for (unsigned int i = (unsigned int)(lane >> 2); i < n; i += (unsigned int)(lanes >> 2)) {
+        int X, t, m;
+        fx Lm[4][4], Rm[4][4], x[5][4];
+        tang_ao_item(P, S, W, rdc(S.itemsT + i, S), X, t, m, Lm, Rm, x);
+        double vq[2], dq[2];
+        tang_ao_x4(Lm, Rm, x, ak, gmask, vq, dq);
+        if (X <= 1) {
+            // positivity of the reconstructed Q^l, Q^r states (gp_positivity), on the gathered components
 #pragma unroll
             for (int g = 0; g < 2; g++) {
-                stc(S.gp + (long long)((g * 6 + qv) * 4 + k) * plane + o, v[k][g], S);
-                if (X <= 1) stc(S.gp + (long long)((g * 6 + qv + 2) * 4 + k) * plane + o, d[k][g] * S.inv_ht, S);
+                double Q[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) Q[k] = __shfl_sync(gmask, vq[g], lane0 + k);
+                if (nonphysical<4>(P.gamma, Q)) { vq[g] = lineval(S, X, q, t, m); dq[g] = 0.0; }
             }
+        }
+        const long long o = (long long)t * S.nm + m;
+        const int qv = X == 0 ? 0 : (X == 1 ? 3 : (X == 2 ? 1 : 4));
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+            stc(S.gp + (long long)((g * 6 + qv) * 4 + q) * plane + o, vq[g], S);
+            if (X <= 1) stc(S.gp + (long long)((g * 6 + qv + 2) * 4 + q) * plane + o, dq[g] * S.inv_ht, S);
         }
     }
 }
@@ -698,15 +772,14 @@ __device__ __forceinline__ void b_tang_ao(const Params& P, const Sweep& S, const
 // (free-order arithmetic).  They are compiled once, as non-inlined functions on a solver
 // descriptor in device memory, and called by both a solver's own kernels and the batched
 // kernels: the same machine code, so batched and solo results are bit-identical by construction.
-__device__ __noinline__ void tang_ao_nl(const SolveDesc& d, int dir, int stage, long long start, long long stride)
+__device__ __noinline__ void tang_ao_nl(const SolveDesc& d, int dir, int stage, long long lane, long long lanes)
 {
-    b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, start, stride);
+    b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, lane, lanes);
 }
 
 __global__ void k_tang_ao(const SolveDesc* __restrict__ D, int dir, int stage)
 {
-    tang_ao_nl(*D, dir, stage, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2,
-               ((long long)gridDim.x * blockDim.x) >> 2);
+    tang_ao_nl(*D, dir, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 
@@ -945,7 +1018,7 @@ template <int NV>
 __global__ void kb_normal_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
 {
     HGKS_BATCH_BLOCK();
-    b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id >> 2, (nblk_ * blockDim.x) >> 2);
+    b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
 }
 
 __global__ void kb_raw_tflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
@@ -963,7 +1036,7 @@ __global__ void kb_tang(const SolveDesc* __restrict__ D, const int* __restrict__
 __global__ void kb_tang_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
 {
     HGKS_BATCH_BLOCK();
-    tang_ao_nl(d, dir, stage, id >> 2, (nblk_ * blockDim.x) >> 2);
+    tang_ao_nl(d, dir, stage, id, nblk_ * blockDim.x);
 }
 
 template <int DIM, int STAGE>

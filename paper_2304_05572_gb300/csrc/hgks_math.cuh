@@ -287,17 +287,32 @@ __device__ __forceinline__ void weno_ao_face(double gam, const AOConst& k, const
 }
 
 #if defined(__CUDACC__)   // lane-group functions: device code only (the host count compiles the flux alone)
+// Row r of M for a per-lane r, selected without indexing local memory.
+template <int NV, typename T>
+__device__ __forceinline__ void select_row(const T (*M)[NV], int r, T* row)
+{
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        T v = M[0][c];
+#pragma unroll
+        for (int k = 1; k < NV; k++) v = r == k ? M[k][c] : v;
+        row[c] = v;
+    }
+}
+
 // The characteristic WENO-AO face reconstruction of weno_ao_face, spread over the 4 lanes of an
 // aligned lane group (lane q = threadIdx.x & 3): lane q projects the window onto characteristic
 // field q (row q of L), runs the nonlinear weights and the AO combination of that field alone,
-// and the 4 fields' results are exchanged with shuffles for the projection back with R.  Every
-// value is formed by the same operations in the same order as in weno_ao_face, so the result
-// (returned in every lane) is bit-identical; the per-lane work, and so the latency of an item
-// on the narrow FP64 pipe, is about a quarter.  Lanes q >= NV (1D) duplicate field NV-1.
-// All 4 lanes of the group must call this together (mask gmask).
+// the 4 fields' results are exchanged with shuffles, and lane q projects back component q (row q
+// of R); the components are exchanged again so that every lane returns the whole state val[]
+// (for the positivity test) and its own component's derivative derq.  Every value is formed by
+// the same operations in the same order as in weno_ao_face, so the results are bit-identical;
+// the per-lane work, and so the latency of an item on the narrow FP64 pipe, is about a quarter.
+// Lanes q >= NV (1D) duplicate field NV-1.  All 4 lanes of the group must call this together
+// (mask gmask).
 template <int NV>
 __device__ __forceinline__ void weno_ao_face_x4(double gam, const AOConst& k, const double (*Qw)[NV], const double* Qs,
-                                                int side, unsigned gmask, double* val, double* der)
+                                                int side, unsigned gmask, double* val, double& derq)
 {
     const int q = threadIdx.x & 3;
     const int qc = q < NV ? q : NV - 1;
@@ -306,14 +321,9 @@ __device__ __forceinline__ void weno_ao_face_x4(double gam, const AOConst& k, co
 #pragma unroll
     for (int c = 0; c < NV; c++) qs[c] = ex(Qs[c]);
     eigvec<NV>(gam, qs, 1.0, 0.0, L, R);
-    ex Lq[NV];
-#pragma unroll
-    for (int c = 0; c < NV; c++) {
-        ex v = L[0][c];
-#pragma unroll
-        for (int r = 1; r < NV; r++) v = qc == r ? L[r][c] : v;
-        Lq[c] = v;
-    }
+    ex Lq[NV], Rq[NV];
+    select_row<NV>(L, qc, Lq);
+    select_row<NV>(R, qc, Rq);
     ex u[5], wb[4], pv[4], pd[4];
 #pragma unroll
     for (int j = 0; j < 5; j++) {
@@ -331,11 +341,13 @@ __device__ __forceinline__ void weno_ao_face_x4(double gam, const AOConst& k, co
         uv[c] = ex(__shfl_sync(gmask, uvq, lane0 + c));
         ud[c] = ex(__shfl_sync(gmask, udq, lane0 + c));
     }
-    ex v[NV], d[NV];
-    matvec<NV>(R, uv, v);
-    matvec<NV>(R, ud, d);
+    // row qc of R times uv and ud, in the summation order of matvec
+    ex v = Rq[0] * uv[0] + Rq[1] * uv[1], d = Rq[0] * ud[0] + Rq[1] * ud[1];
 #pragma unroll
-    for (int c = 0; c < NV; c++) { val[c] = v[c].v; der[c] = d[c].v; }
+    for (int c = 2; c < NV; c++) { v = v + Rq[c] * uv[c]; d = d + Rq[c] * ud[c]; }
+#pragma unroll
+    for (int c = 0; c < NV; c++) val[c] = __shfl_sync(gmask, v.v, lane0 + c);
+    derq = d.v;
 }
 #endif
 
@@ -414,38 +426,23 @@ __device__ __forceinline__ void gauss_ao(const fx* q, const AOConst& k, double* 
     v[0] = a; v[1] = b; d[0] = e; d[1] = f;
 }
 
-#if defined(__CUDACC__)
-// Tangential WENO-AO of one pass (4 components) at the two Gauss points, spread over the 4 lanes
-// of an aligned lane group like weno_ao_face_x4: lane q projects the 5 line values onto field q
-// (row q of Lm), runs gauss_ao for it, and the fields' Gauss-point values and derivatives are
-// exchanged with shuffles; every lane returns the 4 conservative components v[r][g], d[r][g]
-// after the projection back with Rm.  Free-order arithmetic (the outputs only feed the flux).
-__device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4], const fx (*x)[4], const AOConst& ak,
-                                           unsigned gmask, double (*v)[2], double (*d)[2])
+// Tangential WENO-AO of one pass (4 components, one lane) at the two Gauss points: projection of
+// the 5 line values x[s][] onto the characteristic fields (rows of Lm), gauss_ao per field, and
+// the projection back with Rm.  Free-order arithmetic (the outputs only feed the flux).
+__device__ __forceinline__ void tang_ao(const fx (*Lm)[4], const fx (*Rm)[4], const fx (*x)[4], const AOConst& ak,
+                                        double (*v)[2], double (*d)[2])
 {
-    const int q = threadIdx.x & 3;
-    const int lane0 = threadIdx.x & 28;
-    fx Lq[4];
+    // all 20 projections first: the line values are dead before the four fields' weights are
+    // formed (134 registers against 170 with the projection inside the field loop)
+    fx uc[4][5];
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-        fx w = Lm[0][c];
+    for (int s = 0; s < 5; s++)
 #pragma unroll
-        for (int r = 1; r < 4; r++) w = q == r ? Lm[r][c] : w;
-        Lq[c] = w;
-    }
-    fx u[5];
-#pragma unroll
-    for (int s = 0; s < 5; s++) u[s] = xfma(Lq[3], x[s][3], xfma(Lq[2], x[s][2], xfma(Lq[1], x[s][1], Lq[0] * x[s][0])));
-    double cvq[2], cdq[2];
-    gauss_ao(u, ak, cvq, cdq);
+        for (int c = 0; c < 4; c++)
+            uc[c][s] = xfma(Lm[c][3], x[s][3], xfma(Lm[c][2], x[s][2], xfma(Lm[c][1], x[s][1], Lm[c][0] * x[s][0])));
     double cv[4][2], cd[4][2];
 #pragma unroll
-    for (int c = 0; c < 4; c++)
-#pragma unroll
-        for (int g = 0; g < 2; g++) {
-            cv[c][g] = __shfl_sync(gmask, cvq[g], lane0 + c);
-            cd[c][g] = __shfl_sync(gmask, cdq[g], lane0 + c);
-        }
+    for (int c = 0; c < 4; c++) gauss_ao(uc[c], ak, cv[c], cd[c]);
 #pragma unroll
     for (int g = 0; g < 2; g++)
 #pragma unroll
@@ -455,6 +452,36 @@ __device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4],
             for (int c = 0; c < 4; c++) { a = fma(Rm[r][c].v, cv[c][g], a); b = fma(Rm[r][c].v, cd[c][g], b); }
             v[r][g] = a; d[r][g] = b;
         }
+}
+
+#if defined(__CUDACC__)
+// The same pass spread over the 4 lanes of an aligned lane group like weno_ao_face_x4: lane q
+// projects the 5 line values onto field q (row q of Lm), runs gauss_ao for it, the fields'
+// Gauss-point values and derivatives are exchanged with shuffles, and lane q projects back its
+// own component (row q of Rm): vq[g], dq[g] at the two Gauss points.
+__device__ __forceinline__ void tang_ao_x4(const fx (*Lm)[4], const fx (*Rm)[4], const fx (*x)[4], const AOConst& ak,
+                                           unsigned gmask, double* vq, double* dq)
+{
+    const int q = threadIdx.x & 3;
+    const int lane0 = threadIdx.x & 28;
+    fx Lq[4], Rq[4];
+    select_row<4>(Lm, q, Lq);
+    select_row<4>(Rm, q, Rq);
+    fx u[5];
+#pragma unroll
+    for (int s = 0; s < 5; s++) u[s] = xfma(Lq[3], x[s][3], xfma(Lq[2], x[s][2], xfma(Lq[1], x[s][1], Lq[0] * x[s][0])));
+    double cvq[2], cdq[2];
+    gauss_ao(u, ak, cvq, cdq);
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            a = fma(Rq[c].v, __shfl_sync(gmask, cvq[g], lane0 + c), a);
+            b = fma(Rq[c].v, __shfl_sync(gmask, cdq[g], lane0 + c), b);
+        }
+        vq[g] = a; dq[g] = b;
+    }
 }
 #endif
 

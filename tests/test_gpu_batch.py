@@ -25,6 +25,10 @@ def _cases_2d():
     out.append((cfg, W))
     cfg, W, _ = P.viscous_shock_tube(40, 20, Re=300.0)
     out.append((cfg, W))
+    # WENO-AO everywhere at 72x64: every compacted pass holds 9344 to 18688 items, above the size
+    # from which the passes give each item one lane (the others here use lane groups)
+    cfg, W, _ = P.random_smooth_2d(72, 64)
+    out.append((dict(cfg, recon_mode="wenoao"), W))
     return out
 
 
@@ -70,6 +74,9 @@ def test_batch_2d_bitwise_equal_to_alone(graph, autotune):
 def test_batch_1d_and_continuation():
     import torch
     cases = [P.sod_1d(n)[:2] for n in (50, 200, 333)] + [P.blast_1d(120)[:2]]
+    # WENO-AO everywhere on 5000 cells: 10002 troubled sides per pass, one lane each
+    cfg, W, _ = P.sod_1d(5000)
+    cases.append((dict(cfg, recon_mode="wenoao"), W))
     stream = torch.cuda.Stream()
     solvers = []
     for cfg, W in cases:
@@ -77,7 +84,7 @@ def test_batch_1d_and_continuation():
         s.hgks_set_state(np.ascontiguousarray(W))
         solvers.append(s)
     b = hgks.Batch(solvers, stream=stream)
-    t_end = [0.05, 0.02, 0.2, 0.01]
+    t_end = [0.05, 0.02, 0.2, 0.01, 0.002]
     for _ in range(4):                    # several calls continue where the last stopped
         b.hgks_batch_step(t_end, nsteps=5, graph=True)
     b.hgks_batch_sync()

@@ -162,6 +162,17 @@ def test_recon_modes_2d(mode):
     check_step(cfg, W, mode)
 
 
+@pytest.mark.parametrize("nx,ny", [(24, 20), (72, 64)])
+def test_wenoao_passes_in_both_lane_forms(nx, ny):
+    """WENO-AO everywhere: at 24x20 every compacted pass holds fewer than 8192 items and runs
+    one item per group of 4 lanes; at 72x64 every pass holds 9344 to 18688 items and runs one
+    item per lane.  Both match the oracle step by step."""
+    cfg, W, _ = P.random_smooth_2d(nx, ny)
+    cfg["recon_mode"] = "wenoao"
+    Wo, _, _, _ = check_step(cfg, W, "wenoao %dx%d" % (nx, ny))
+    check_step(cfg, Wo, "wenoao %dx%d, second step" % (nx, ny))
+
+
 def test_paper_riemann_configurations():
     for fn in (P.riemann_config1, P.riemann_config6):
         cfg, W, _ = fn(40)
@@ -278,6 +289,40 @@ def test_nonphysical_state_is_reported():
     assert e.value.code == hgks.HGKS_ENONPHYSICAL
     assert s.hgks_get_stats()["status"] == hgks.HGKS_ENONPHYSICAL
     s.hgks_destroy_solver()
+
+
+@pytest.mark.parametrize("k,n", [(3, 32), (214, 40), (224, 48)])
+def test_breakdown_at_the_oracles_step(k, n):
+    """Seeded four-quadrant states of the batched workload whose solution loses positivity
+    (the scheme has no positivity limiter; the oracle's pressure minimum falls to ~3e-3 the step
+    before): stepped one step at a time, the GPU reports HGKS_ENONPHYSICAL at the same step as
+    the oracle, and the last physical states agree.  The breakdown sits at the quadrants'
+    corner, so its step does not depend on the grid (these seeds break at steps 6, 6 and 7
+    at their 928^2, 442^2 and 964^2 batched sizes too)."""
+    cfg, W, _ = P.riemann4_2d(n, seed=P.BATCH_SEED + 1 + k)
+    s = hgks.Solver(cfg)
+    s.hgks_set_state(np.ascontiguousarray(W))
+    Wg, step_gpu = None, None
+    for j in range(1, 20):
+        try:
+            s.hgks_step(1e300, 1)
+        except hgks.HGKSError as e:
+            assert e.code == hgks.HGKS_ENONPHYSICAL
+            step_gpu = j
+            break
+        Wg = s.hgks_get_state()
+    s.hgks_destroy_solver()
+    Wo, step_or = np.ascontiguousarray(W), None
+    for j in range(1, 20):
+        try:
+            Wn, _, _, _ = oracle.run(cfg, Wo, 1e300, max_steps=1)
+        except RuntimeError as e:
+            assert "status -3" in str(e)
+            step_or = j
+            break
+        Wo = Wn
+    assert step_gpu is not None and step_gpu == step_or, (step_gpu, step_or)
+    assert rel_diff(Wg, Wo) <= FINAL_TOL
 
 
 def test_troubled_counters():
