@@ -92,7 +92,8 @@ int validate(const hgks_config* c, char* err)
 
 struct Layout {
     size_t total;
-    size_t off_W, off_Ws, off_Acc, off_ctrl, off_desc, off_line, off_gp;
+    size_t off_W, off_Ws, off_Acc, off_ctrl, off_desc;
+    size_t off_line[2], off_gp[2];
     size_t off_rawN[2], off_flagN[2], off_rawT[2], off_flagT[2], off_itemsN[2], off_itemsT[2], off_flux[2];
 };
 
@@ -168,16 +169,11 @@ Layout plan(const hgks_config* c, const Params& P, const Sweep* sw)
     L.off_ctrl = take(sizeof(Ctrl));
     L.off_desc = take(sizeof(SolveDesc));
     int nd = c->dim;
-    size_t maxline = 0, maxgp = 0;
+    // every buffer a sweep writes is its own: the two sweeps of a stage run in the same launches
     for (int d = 0; d < nd; d++) {
         const Sweep& S = sw[d];
-        maxline = std::max(maxline, (size_t)S.nlines * S.nm);
-        maxgp = std::max(maxgp, (size_t)S.nt * S.nm);
-    }
-    L.off_line = take((size_t)4 * P.g.nv * maxline * sizeof(double));
-    L.off_gp = c->dim == 2 ? take((size_t)2 * 6 * 4 * maxgp * sizeof(double)) : 0;
-    for (int d = 0; d < nd; d++) {
-        const Sweep& S = sw[d];
+        L.off_line[d] = take((size_t)4 * P.g.nv * S.nlines * S.nm * sizeof(double));
+        L.off_gp[d] = c->dim == 2 ? take((size_t)2 * 6 * 4 * S.nt * S.nm * sizeof(double)) : 0;
         L.off_rawN[d] = take((size_t)S.nlines * (S.nn + 4));
         L.off_flagN[d] = take((size_t)S.nlines * (S.nn + 2));
         L.off_itemsN[d] = take((size_t)S.nlines * S.nm * 2 * sizeof(uint32_t));
@@ -271,8 +267,8 @@ extern "C" int hgks_create_solver(const hgks_config* cfg, void* stream, hgks_sol
     s->ctrl = (Ctrl*)(base + L.off_ctrl);
     for (int d = 0; d < cfg->dim; d++) {
         Sweep& S = s->sw[d];
-        S.line = (double*)(base + L.off_line);
-        S.gp = cfg->dim == 2 ? (double*)(base + L.off_gp) : nullptr;
+        S.line = (double*)(base + L.off_line[d]);
+        S.gp = cfg->dim == 2 ? (double*)(base + L.off_gp[d]) : nullptr;
         S.rawN = (uint8_t*)(base + L.off_rawN[d]);
         S.flagN = (uint8_t*)(base + L.off_flagN[d]);
         S.itemsN = (uint32_t*)(base + L.off_itemsN[d]);
@@ -546,7 +542,7 @@ int batch_reserve(hgks_batch* b, int n)
     if (b->h_tend) cudaFreeHost(b->h_tend);
     b->d_desc = nullptr; b->d_boff = nullptr; b->d_tend = nullptr; b->h_tend = nullptr; b->cap = 0;
     cudaError_t e = cudaMalloc(&b->d_desc, sizeof(SolveDesc) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_boff, sizeof(int) * (size_t)BK_COUNT * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_boff, sizeof(int) * (size_t)BK_COUNT * (2 * (size_t)cap + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tend, sizeof(double) * cap);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tend, sizeof(double) * cap);
     if (e != cudaSuccess) { set_err(b->err, "batch allocation failed: %s", cudaGetErrorString(e)); return HGKS_ENOMEM; }
@@ -674,7 +670,7 @@ extern "C" int hgks_batch_step(hgks_batch* b, const double* t_end, int nsteps, i
         for (int k = 0; k < 3 && left > 0; k++) {
             int tpb[BK_COUNT];
             for (int c = 0; c < BK_COUNT; c++) {
-                bool heavy_regs = (c >= BK_FLUX && c < BK_FLUX + 2) || (c >= BK_NAO && c < BK_NAO + 2) || (c >= BK_TAO && c < BK_TAO + 2);
+                bool heavy_regs = c == BK_FLUX || c == BK_NAO || c == BK_TAO;
                 tpb[c] = c == BK_CTRL ? 32 : (heavy_regs ? cand_small[k] : cand_big[k]);
             }
             int st = batch_upload_plan(b, tpb);
@@ -904,8 +900,8 @@ extern "C" int hgks_step_noalloc(const hgks_config* cfg, const double* W_in, dou
     s.ctrl = (Ctrl*)(b + L.off_ctrl);
     for (int d = 0; d < cfg->dim; d++) {
         Sweep& S = s.sw[d];
-        S.line = (double*)(b + L.off_line);
-        S.gp = cfg->dim == 2 ? (double*)(b + L.off_gp) : nullptr;
+        S.line = (double*)(b + L.off_line[d]);
+        S.gp = cfg->dim == 2 ? (double*)(b + L.off_gp[d]) : nullptr;
         S.rawN = (uint8_t*)(b + L.off_rawN[d]);
         S.flagN = (uint8_t*)(b + L.off_flagN[d]);
         S.itemsN = (uint32_t*)(b + L.off_itemsN[d]);

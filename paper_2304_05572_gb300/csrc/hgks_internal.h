@@ -90,18 +90,22 @@ struct SolveDesc {
     double h;          // min(dx, dy): the CFL length
 };
 
-// Kernel classes of a batched step.  Classes with a sweep index have one entry per sweep.
+// Kernel classes of a batched step, one launch each per stage.  The sweep classes (BK_RAWN to
+// BK_FLUX) cover both sweeps of every solver: their units are (solver s, sweep d), unit 2 s + d.
 enum BatchClass {
     BK_CTRL = 0, BK_DT, BK_GHX, BK_GHY,
-    BK_RAWN, BK_NORMAL = BK_RAWN + 2, BK_NAO = BK_NORMAL + 2, BK_RAWT = BK_NAO + 2, BK_TANG = BK_RAWT + 2,
-    BK_TAO = BK_TANG + 2, BK_FLUX = BK_TAO + 2, BK_UPD = BK_FLUX + 2, BK_COUNT
+    BK_RAWN, BK_NORMAL, BK_NAO, BK_RAWT, BK_TANG, BK_TAO, BK_FLUX,
+    BK_UPD, BK_COUNT
 };
+
+inline bool batch_sweep_class(int c) { return c >= BK_RAWN && c <= BK_FLUX; }
 
 struct BatchPlan {
     int n = 0, dim = 0;
     int tpb[BK_COUNT];
     int nblk[BK_COUNT];            // total blocks of each class
-    std::vector<int> boff;         // [BK_COUNT][n + 1] block offsets per solver
+    std::vector<int> boff;         // [BK_COUNT][2 n + 1] block offsets per unit (a solver, or a
+                                   // solver's sweep for the sweep classes)
 };
 
 }  // namespace hgks

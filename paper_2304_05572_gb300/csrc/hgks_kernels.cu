@@ -291,10 +291,29 @@ __device__ __forceinline__ void b_raw_nflags(const Params& P, const Sweep& S, co
     stc(S.rawN + id, tr, S);
 }
 
-template <int NV>
-__global__ void k_raw_nflags(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+// A solver's own sweep kernels run the two sweeps of a 2D stage in one launch (they share no
+// buffer and no result until the update): blocks [0, nb0) work on the x sweep, the others on the
+// y sweep; 1D launches give every block to the x sweep.  `id` is the thread's index within its
+// sweep's blocks, `lanes` the number of threads on that sweep.
+struct SweepBlock { int dir; long long id, lanes; };
+
+__device__ __forceinline__ SweepBlock sweep_block(int nb0)
 {
-    b_raw_nflags<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    SweepBlock r;
+    r.dir = (int)blockIdx.x >= nb0 ? 1 : 0;
+    const long long first = r.dir ? nb0 : 0;
+    const long long nb = r.dir ? (long long)gridDim.x - nb0 : (long long)nb0;
+    r.id = ((long long)blockIdx.x - first) * blockDim.x + threadIdx.x;
+    r.lanes = nb * blockDim.x;
+    return r;
+}
+
+template <int NV>
+__global__ void k_raw_nflags(const SolveDesc* __restrict__ D, int nb0, int stage)
+{
+    const SweepBlock b = sweep_block(nb0);
+    const SolveDesc& d = *D;
+    b_raw_nflags<NV>(d.P, d.sw[b.dir], stage == 0 ? d.W : d.Ws, d.ctrl, b.id);
 }
 
 
@@ -365,9 +384,11 @@ __device__ __forceinline__ void b_normal(const Params& P, const Sweep& S, const 
 }
 
 template <int NV>
-__global__ void k_normal(Params P, Sweep S, const double* __restrict__ W, Ctrl* ctrl, int stage)
+__global__ void k_normal(const SolveDesc* __restrict__ D, int nb0, int stage)
 {
-    b_normal<NV>(P, S, W, ctrl, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const SweepBlock b = sweep_block(nb0);
+    const SolveDesc& d = *D;
+    b_normal<NV>(d.P, d.sw[b.dir], stage == 0 ? d.W : d.Ws, d.ctrl, stage, b.id);
 }
 
 
@@ -460,9 +481,11 @@ __device__ __forceinline__ void b_normal_ao(const Params& P, const Sweep& S, con
 }
 
 template <int NV>
-__global__ void k_normal_ao(Params P, Sweep S, const double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_normal_ao(const SolveDesc* __restrict__ D, int nb0, int stage)
 {
-    b_normal_ao<NV>(P, S, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    const SweepBlock b = sweep_block(nb0);
+    const SolveDesc& d = *D;
+    b_normal_ao<NV>(d.P, d.sw[b.dir], stage == 0 ? d.W : d.Ws, d.ctrl, b.id, b.lanes);
 }
 
 
@@ -535,9 +558,11 @@ __device__ __forceinline__ void b_raw_tflags(const Params& P, const Sweep& S, co
     else b_raw_tflags_x1(P, S, ctrl, id);
 }
 
-__global__ void k_raw_tflags(Params P, Sweep S, const Ctrl* __restrict__ ctrl)
+__global__ void k_raw_tflags(const SolveDesc* __restrict__ D, int nb0)
 {
-    b_raw_tflags(P, S, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const SweepBlock b = sweep_block(nb0);
+    const SolveDesc& d = *D;
+    b_raw_tflags(d.P, d.sw[b.dir], d.ctrl, b.id);
 }
 
 
@@ -676,9 +701,11 @@ __device__ __forceinline__ void b_tang(const Params& P, const Sweep& S, Ctrl* ct
     else b_tflags_x1(P, S, ctrl, stage, id);
 }
 
-__global__ void k_tang(Params P, Sweep S, Ctrl* ctrl, int stage)
+__global__ void k_tang(const SolveDesc* __restrict__ D, int nb0, int stage)
 {
-    b_tang(P, S, ctrl, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const SweepBlock b = sweep_block(nb0);
+    const SolveDesc& d = *D;
+    b_tang(d.P, d.sw[b.dir], d.ctrl, stage, b.id);
 }
 
 
@@ -777,9 +804,10 @@ __device__ __noinline__ void tang_ao_nl(const SolveDesc& d, int dir, int stage, 
     b_tang_ao(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, lane, lanes);
 }
 
-__global__ void k_tang_ao(const SolveDesc* __restrict__ D, int dir, int stage)
+__global__ void k_tang_ao(const SolveDesc* __restrict__ D, int nb0, int stage)
 {
-    tang_ao_nl(*D, dir, stage, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    const SweepBlock b = sweep_block(nb0);
+    tang_ao_nl(*D, b.dir, stage, b.id, b.lanes);
 }
 
 
@@ -864,9 +892,10 @@ __device__ __noinline__ void flux_nl(const SolveDesc& d, int dir, long long id)
 // 8 warps per SM) lets the flux keep its working set in registers (measured 3.5 % faster than
 // under a 128-thread bound at the same occupancy)
 template <int DIM, int STAGE, bool PRFIX>
-__global__ void __launch_bounds__(64, 4) k_flux(const SolveDesc* __restrict__ D, int dir)
+__global__ void __launch_bounds__(64, 4) k_flux(const SolveDesc* __restrict__ D, int nb0)
 {
-    flux_nl<DIM, STAGE, PRFIX>(*D, dir, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const SweepBlock b = sweep_block(nb0);
+    flux_nl<DIM, STAGE, PRFIX>(*D, b.dir, b.id);
 }
 
 // Stage 0: W* = W^n - dF(dt/2)/dx - dG(dt/2)/dy (Eq. (19)), Acc = W^n - d(dt F^n + dt^2/6 dF^n)/dx - ...
@@ -957,6 +986,16 @@ __device__ __forceinline__ int find_solve(const int* __restrict__ boff, int n, i
     const long long id = lblk_ * blockDim.x + threadIdx.x;                               \
     (void)nblk_; (void)id;
 
+// sweep classes: the units are (solver, sweep) pairs, unit u = 2 s + dir; n counts solvers
+#define HGKS_BATCH_SWEEP_BLOCK()                                                        \
+    const int u_ = find_solve(boff, 2 * n, (int)blockIdx.x);                             \
+    const SolveDesc& d = D[u_ >> 1];                                                     \
+    const int dir = u_ & 1;                                                              \
+    const long long lblk_ = (long long)blockIdx.x - boff[u_];                            \
+    const long long nblk_ = (long long)(boff[u_ + 1] - boff[u_]);                         \
+    const long long id = lblk_ * blockDim.x + threadIdx.x;                               \
+    (void)nblk_; (void)id;
+
 __global__ void kb_ctrl(const SolveDesc* __restrict__ D, int n, int what, const double* __restrict__ tend)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1001,48 +1040,48 @@ __global__ void kb_ghost(const SolveDesc* __restrict__ D, const int* __restrict_
 }
 
 template <int NV>
-__global__ void kb_raw_nflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+__global__ void kb_raw_nflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     b_raw_nflags<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id);
 }
 
 template <int NV>
-__global__ void kb_normal(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+__global__ void kb_normal(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     b_normal<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, stage, id);
 }
 
 template <int NV>
-__global__ void kb_normal_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+__global__ void kb_normal_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     b_normal_ao<NV>(d.P, d.sw[dir], stage == 0 ? d.W : d.Ws, d.ctrl, id, nblk_ * blockDim.x);
 }
 
-__global__ void kb_raw_tflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
+__global__ void kb_raw_tflags(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     b_raw_tflags(d.P, d.sw[dir], d.ctrl, id);
 }
 
-__global__ void kb_tang(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+__global__ void kb_tang(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     b_tang(d.P, d.sw[dir], d.ctrl, stage, id);
 }
 
-__global__ void kb_tang_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage, int dir)
+__global__ void kb_tang_ao(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int stage)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     tang_ao_nl(d, dir, stage, id, nblk_ * blockDim.x);
 }
 
 template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256) kb_flux(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n, int dir)
+__global__ void __launch_bounds__(256) kb_flux(const SolveDesc* __restrict__ D, const int* __restrict__ boff, int n)
 {
-    HGKS_BATCH_BLOCK();
+    HGKS_BATCH_SWEEP_BLOCK();
     if (d.P.prfix != 0.0) flux_nl<DIM, STAGE, true>(d, dir, id);
     else flux_nl<DIM, STAGE, false>(d, dir, id);
 }
@@ -1134,59 +1173,70 @@ static void timed(hgks_solver* s, int cls, int nkernels, F&& launch)
     s->timers.push_back(TimerRec{cls, a, b});
 }
 
+// The sweep kernels of one stage, each class one launch over both sweeps (2D): nb[0] blocks for
+// the x sweep, then nb[1] for the y sweep.
 template <int DIM>
-static void enqueue_sweep(hgks_solver* s, int d, int stage, const double* Win)
+static void enqueue_sweeps(hgks_solver* s, int stage)
 {
     const Params& P = s->P;
-    Sweep& S = s->sw[d];
     cudaStream_t st = s->stream;
-    Ctrl* ctrl = s->ctrl;
+    const SolveDesc* D = s->d_self;
     constexpr int NV = DIM + 2;
-    int sms = device_sm_count();
+    const int sms = device_sm_count();
+    auto pair = [&](auto blocks, unsigned int* nb) {
+        nb[0] = blocks(s->sw[0]);
+        nb[1] = DIM == 2 ? blocks(s->sw[1]) : 0u;
+        return nb[0] + nb[1];
+    };
+    // the compacted WENO-AO passes: a grid for 4 lanes per possible item, capped at 8 blocks per SM
+    auto ao_blocks = [&](long long maxn) {
+        unsigned int b = blocks_for(maxn, 128);
+        return b > (unsigned)(sms * 8) ? (unsigned)(sms * 8) : b;
+    };
+    unsigned int nb[2];
     timed(s, KC_RAWN, 1, [&] {
-        long long n = (long long)S.nlines * (S.nn + 4);
-        k_raw_nflags<NV><<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, Win, ctrl);
+        unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)S.nlines * (S.nn + 4), TPB); }, nb);
+        k_raw_nflags<NV><<<g, TPB, 0, st>>>(D, (int)nb[0], stage);
     });
     timed(s, KC_NORMAL, 1, [&] {
-        long long n = (long long)S.nlines * S.nm;
-        k_normal<NV><<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, Win, ctrl, stage);
+        unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)S.nlines * S.nm, TPB); }, nb);
+        k_normal<NV><<<g, TPB, 0, st>>>(D, (int)nb[0], stage);
     });
     timed(s, KC_NORMAL_AO, 1, [&] {
-        long long maxn = (long long)S.nlines * S.nm * 2 * 4;     // 4 lanes per item
-        unsigned int b = blocks_for(maxn, 128);
-        if (b > (unsigned)(sms * 8)) b = sms * 8;
-        k_normal_ao<NV><<<b, 128, 0, st>>>(P, S, Win, ctrl);
+        unsigned int g = pair([&](const Sweep& S) { return ao_blocks((long long)S.nlines * S.nm * 2 * 4); }, nb);
+        k_normal_ao<NV><<<g, 128, 0, st>>>(D, (int)nb[0], stage);
     });
     if constexpr (DIM == 2) {
         timed(s, KC_RAWT, 1, [&] {
-            long long n = (long long)(S.nt + 2) * S.nm * S.tlanes;
-            k_raw_tflags<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl);
+            unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)(S.nt + 2) * S.nm * S.tlanes, TPB); }, nb);
+            k_raw_tflags<<<g, TPB, 0, st>>>(D, (int)nb[0]);
         });
         timed(s, KC_TANG, 1, [&] {
-            long long n = (long long)S.nt * S.nm * S.tlanes;
-            k_tang<<<blocks_for(n, TPB), TPB, 0, st>>>(P, S, ctrl, stage);
+            unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)S.nt * S.nm * S.tlanes, TPB); }, nb);
+            k_tang<<<g, TPB, 0, st>>>(D, (int)nb[0], stage);
         });
         timed(s, KC_TANG_AO, 1, [&] {
-            long long maxn = (long long)S.nt * S.nm * 4 * 4;     // 4 lanes per item
-            unsigned int b = blocks_for(maxn, 128);
-            if (b > (unsigned)(sms * 8)) b = sms * 8;
-            k_tang_ao<<<b, 128, 0, st>>>(s->d_self, d, stage);
+            unsigned int g = pair([&](const Sweep& S) { return ao_blocks((long long)S.nt * S.nm * 4 * 4); }, nb);
+            k_tang_ao<<<g, 128, 0, st>>>(D, (int)nb[0], stage);
         });
     }
     if (s->capture) {
-        size_t nb = (size_t)S.nlines * (S.nn + 2);
-        cudaMemcpyAsync(s->cap[stage][d][0], S.flagN, nb, cudaMemcpyDeviceToDevice, st);
-        if (DIM == 2) cudaMemcpyAsync(s->cap[stage][d][1], S.flagT, (size_t)S.nt * S.nm, cudaMemcpyDeviceToDevice, st);
+        for (int d = 0; d < DIM; d++) {
+            const Sweep& S = s->sw[d];
+            size_t nbytes = (size_t)S.nlines * (S.nn + 2);
+            cudaMemcpyAsync(s->cap[stage][d][0], S.flagN, nbytes, cudaMemcpyDeviceToDevice, st);
+            if (DIM == 2) cudaMemcpyAsync(s->cap[stage][d][1], S.flagT, (size_t)S.nt * S.nm, cudaMemcpyDeviceToDevice, st);
+        }
     }
     timed(s, KC_FLUX, 1, [&] {
-        long long n = (long long)S.nt * S.nm * (DIM == 2 ? 2 : 1);
-        const unsigned int nb = blocks_for(n, 64);
+        unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)S.nt * S.nm * (DIM == 2 ? 2 : 1), 64); }, nb);
+        const int n0 = (int)nb[0];
         if (P.prfix != 0.0) {
-            if (stage == 0) k_flux<DIM, 0, true><<<nb, 64, 0, st>>>(s->d_self, d);
-            else k_flux<DIM, 1, true><<<nb, 64, 0, st>>>(s->d_self, d);
+            if (stage == 0) k_flux<DIM, 0, true><<<g, 64, 0, st>>>(D, n0);
+            else k_flux<DIM, 1, true><<<g, 64, 0, st>>>(D, n0);
         } else {
-            if (stage == 0) k_flux<DIM, 0, false><<<nb, 64, 0, st>>>(s->d_self, d);
-            else k_flux<DIM, 1, false><<<nb, 64, 0, st>>>(s->d_self, d);
+            if (stage == 0) k_flux<DIM, 0, false><<<g, 64, 0, st>>>(D, n0);
+            else k_flux<DIM, 1, false><<<g, 64, 0, st>>>(D, n0);
         }
     });
 }
@@ -1204,8 +1254,7 @@ static void enqueue_stage(hgks_solver* s, int stage)
         k_ghost_x<<<blocks_for((long long)P.g.nv * rowsI * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
         if (DIM == 2) k_ghost_y<<<blocks_for((long long)P.g.nv * (P.g.nx + 2 * NG) * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl, stage);
     });
-    enqueue_sweep<DIM>(s, 0, stage, Win);
-    if (DIM == 2) enqueue_sweep<DIM>(s, 1, stage, Win);
+    enqueue_sweeps<DIM>(s, stage);
     timed(s, KC_UPDATE, 1, [&] {
         long long n = (long long)(DIM == 2 ? P.g.ny : 1) * P.g.nx;
         if (stage == 0) k_update<DIM, 0><<<blocks_for(n, TPB), TPB, 0, st>>>(P, s->sw[0], s->sw[1], s->W, s->Ws, s->Acc, s->ctrl);
@@ -1240,13 +1289,13 @@ cudaError_t launch_step(hgks_solver* s, double t_end)
 // ---------------------------------------------------------------- host: batched step
 const int kBatchTpbDefault[BK_COUNT] = {
     32, 256, 256, 256,        // ctrl, dt, ghost x, ghost y
-    256, 256,                 // raw normal flags (x, y)
-    256, 256,                 // normal reconstruction
-    128, 128,                 // normal WENO-AO
-    256, 256,                 // raw tangential flags
-    256, 256,                 // tangential reconstruction
-    128, 128,                 // tangential WENO-AO
-    128, 128,                 // flux
+    256,                      // raw normal flags
+    256,                      // normal reconstruction
+    128,                      // normal WENO-AO
+    256,                      // raw tangential flags
+    256,                      // tangential reconstruction
+    128,                      // tangential WENO-AO
+    128,                      // flux
     256                       // update
 };
 
@@ -1262,45 +1311,50 @@ void batch_fill_desc(const hgks_solver* s, SolveDesc& d)
     d.h = s->P.g.dim == 2 ? (s->P.g.dx < s->P.g.dy ? s->P.g.dx : s->P.g.dy) : s->P.g.dx;
 }
 
+// Blocks of one unit of class c with t threads per block: solver d (sweep dir for the sweep classes).
+static long long batch_unit_blocks(const SolveDesc& d, int dim, int c, int dir, int t)
+{
+    const GridGeom& g = d.P.g;
+    const Sweep& S = d.sw[dir];
+    const long long cells = (long long)(dim == 2 ? g.ny : 1) * g.nx;
+    if (batch_sweep_class(c) && dir >= dim) return 0;          // 1D: no y sweep
+    long long b = 0;
+    switch (c) {
+        case BK_CTRL: return 0;
+        case BK_DT: b = (cells + (long long)t * 8 - 1) / ((long long)t * 8); break;
+        case BK_GHX: b = blocks_for((long long)g.nv * (dim == 2 ? g.ny : 1) * NG * 2, t); break;
+        case BK_GHY: if (dim != 2) return 0; b = blocks_for((long long)g.nv * (g.nx + 2 * NG) * NG * 2, t); break;
+        case BK_RAWN: b = blocks_for((long long)S.nlines * (S.nn + 4), t); break;
+        case BK_NORMAL: b = blocks_for((long long)S.nlines * S.nm, t); break;
+        case BK_NAO: b = blocks_for((long long)S.nlines * S.nm * 2 * 4, t * 8); break;
+        case BK_RAWT: if (dim != 2) return 0; b = blocks_for((long long)(S.nt + 2) * S.nm * S.tlanes, t); break;
+        case BK_TANG: if (dim != 2) return 0; b = blocks_for((long long)S.nt * S.nm * S.tlanes, t); break;
+        case BK_TAO: if (dim != 2) return 0; b = blocks_for((long long)S.nt * S.nm * 4 * 4, t * 8); break;
+        case BK_FLUX: b = blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t); break;
+        case BK_UPD: b = blocks_for(cells, t); break;
+    }
+    return b < 1 ? 1 : b;
+}
+
 void batch_plan(const std::vector<const SolveDesc*>& descs, int dim, const int* tpb, BatchPlan& plan)
 {
     const int n = (int)descs.size();
+    const size_t stride = (size_t)2 * n + 1;
     plan.n = n;
     plan.dim = dim;
     for (int c = 0; c < BK_COUNT; c++) plan.tpb[c] = tpb[c];
-    plan.boff.assign((size_t)BK_COUNT * (n + 1), 0);
+    plan.boff.assign((size_t)BK_COUNT * stride, 0);
     for (int c = 0; c < BK_COUNT; c++) {
-        int* bo = plan.boff.data() + (size_t)c * (n + 1);
+        int* bo = plan.boff.data() + (size_t)c * stride;
+        const bool sw = batch_sweep_class(c);
+        const int units = sw ? 2 * n : n;
         long long acc = 0;
-        for (int s = 0; s < n; s++) {
-            const SolveDesc& d = *descs[s];
-            const GridGeom& g = d.P.g;
-            const int t = tpb[c];
-            const long long cells = (long long)(dim == 2 ? g.ny : 1) * g.nx;
-            long long b = 0;
-            int dir = 0;
-            if (c >= BK_RAWN && c < BK_UPD) dir = (c - BK_RAWN) % 2;
-            const Sweep& S = d.sw[dir];
-            const bool sweep_used = dir == 0 || dim == 2;
-            switch (c >= BK_RAWN && c < BK_UPD ? BK_RAWN + ((c - BK_RAWN) / 2) * 2 : c) {
-                case BK_CTRL: b = 0; break;
-                case BK_DT: b = (cells + (long long)t * 8 - 1) / ((long long)t * 8); break;
-                case BK_GHX: b = blocks_for((long long)g.nv * (dim == 2 ? g.ny : 1) * NG * 2, t); break;
-                case BK_GHY: b = dim == 2 ? blocks_for((long long)g.nv * (g.nx + 2 * NG) * NG * 2, t) : 0; break;
-                case BK_RAWN: b = sweep_used ? blocks_for((long long)S.nlines * (S.nn + 4), t) : 0; break;
-                case BK_NORMAL: b = sweep_used ? blocks_for((long long)S.nlines * S.nm, t) : 0; break;
-                case BK_NAO: b = sweep_used ? blocks_for((long long)S.nlines * S.nm * 2 * 4, t * 8) : 0; break;
-                case BK_RAWT: b = dim == 2 ? blocks_for((long long)(S.nt + 2) * S.nm * S.tlanes, t) : 0; break;
-                case BK_TANG: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * S.tlanes, t) : 0; break;
-                case BK_TAO: b = dim == 2 ? blocks_for((long long)S.nt * S.nm * 4 * 4, t * 8) : 0; break;
-                case BK_FLUX: b = sweep_used ? blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t) : 0; break;
-                case BK_UPD: b = blocks_for(cells, t); break;
-            }
-            if (b < 1 && c != BK_CTRL && !(c == BK_GHY && dim == 1) && b == 0 && sweep_used) b = 1;
-            bo[s] = (int)acc;
-            acc += b;
+        for (int u = 0; u < units; u++) {
+            bo[u] = (int)acc;
+            acc += sw ? batch_unit_blocks(*descs[u >> 1], dim, c, u & 1, tpb[c])
+                      : batch_unit_blocks(*descs[u], dim, c, 0, tpb[c]);
         }
-        bo[n] = (int)acc;
+        bo[units] = (int)acc;
         plan.nblk[c] = c == BK_CTRL ? (int)blocks_for(n, tpb[c]) : (int)acc;
     }
 }
@@ -1311,62 +1365,62 @@ cudaError_t batch_enqueue_step(const BatchPlan& plan, const SolveDesc* dd, const
     NvtxRange range("hgks_batch_step");
     const int n = plan.n;
     const int dim = plan.dim;
-    auto bo = [&](int c) { return dboff + (size_t)c * (n + 1); };
+    auto bo = [&](int c) { return dboff + (size_t)c * (2 * n + 1); };
     auto mark = [&](int c, int which) { if (ev) cudaEventRecord(ev[2 * c + which], st); };
     auto grid = [&](int c) { return (unsigned int)plan.nblk[c]; };
+    auto tp = [&](int c) { return plan.tpb[c]; };
     const int tc = plan.tpb[BK_CTRL];
     kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 0, dtend);
     mark(BK_DT, 0);
-    if (grid(BK_DT)) kb_dt<<<grid(BK_DT), plan.tpb[BK_DT], 0, st>>>(dd, bo(BK_DT), n);
+    if (grid(BK_DT)) kb_dt<<<grid(BK_DT), tp(BK_DT), 0, st>>>(dd, bo(BK_DT), n);
     mark(BK_DT, 1);
     kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 1, dtend);
     for (int stage = 0; stage < 2; stage++) {
         kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 2, dtend);
         mark(BK_GHX, 0);
-        kb_ghost<<<grid(BK_GHX), plan.tpb[BK_GHX], 0, st>>>(dd, bo(BK_GHX), n, stage, 0);
+        kb_ghost<<<grid(BK_GHX), tp(BK_GHX), 0, st>>>(dd, bo(BK_GHX), n, stage, 0);
         mark(BK_GHX, 1);
         if (dim == 2) {
             mark(BK_GHY, 0);
-            kb_ghost<<<grid(BK_GHY), plan.tpb[BK_GHY], 0, st>>>(dd, bo(BK_GHY), n, stage, 1);
+            kb_ghost<<<grid(BK_GHY), tp(BK_GHY), 0, st>>>(dd, bo(BK_GHY), n, stage, 1);
             mark(BK_GHY, 1);
         }
-        for (int dir = 0; dir < dim; dir++) {
-            mark(BK_RAWN + dir, 0);
-            if (dim == 2) kb_raw_nflags<4><<<grid(BK_RAWN + dir), plan.tpb[BK_RAWN + dir], 0, st>>>(dd, bo(BK_RAWN + dir), n, stage, dir);
-            else kb_raw_nflags<3><<<grid(BK_RAWN + dir), plan.tpb[BK_RAWN + dir], 0, st>>>(dd, bo(BK_RAWN + dir), n, stage, dir);
-            mark(BK_RAWN + dir, 1);
-            mark(BK_NORMAL + dir, 0);
-            if (dim == 2) kb_normal<4><<<grid(BK_NORMAL + dir), plan.tpb[BK_NORMAL + dir], 0, st>>>(dd, bo(BK_NORMAL + dir), n, stage, dir);
-            else kb_normal<3><<<grid(BK_NORMAL + dir), plan.tpb[BK_NORMAL + dir], 0, st>>>(dd, bo(BK_NORMAL + dir), n, stage, dir);
-            mark(BK_NORMAL + dir, 1);
-            mark(BK_NAO + dir, 0);
-            if (dim == 2) kb_normal_ao<4><<<grid(BK_NAO + dir), plan.tpb[BK_NAO + dir], 0, st>>>(dd, bo(BK_NAO + dir), n, stage, dir);
-            else kb_normal_ao<3><<<grid(BK_NAO + dir), plan.tpb[BK_NAO + dir], 0, st>>>(dd, bo(BK_NAO + dir), n, stage, dir);
-            mark(BK_NAO + dir, 1);
-            if (dim == 2) {
-                mark(BK_RAWT + dir, 0);
-                kb_raw_tflags<<<grid(BK_RAWT + dir), plan.tpb[BK_RAWT + dir], 0, st>>>(dd, bo(BK_RAWT + dir), n, dir);
-                mark(BK_RAWT + dir, 1);
-                mark(BK_TANG + dir, 0);
-                kb_tang<<<grid(BK_TANG + dir), plan.tpb[BK_TANG + dir], 0, st>>>(dd, bo(BK_TANG + dir), n, stage, dir);
-                mark(BK_TANG + dir, 1);
-                mark(BK_TAO + dir, 0);
-                kb_tang_ao<<<grid(BK_TAO + dir), plan.tpb[BK_TAO + dir], 0, st>>>(dd, bo(BK_TAO + dir), n, stage, dir);
-                mark(BK_TAO + dir, 1);
-            }
-            mark(BK_FLUX + dir, 0);
-            const int tf = plan.tpb[BK_FLUX + dir];
-            if (dim == 2) {
-                if (stage == 0) kb_flux<2, 0><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
-                else kb_flux<2, 1><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
-            } else {
-                if (stage == 0) kb_flux<1, 0><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
-                else kb_flux<1, 1><<<grid(BK_FLUX + dir), tf, 0, st>>>(dd, bo(BK_FLUX + dir), n, dir);
-            }
-            mark(BK_FLUX + dir, 1);
+        // every sweep class: one launch over both sweeps of every solver
+        mark(BK_RAWN, 0);
+        if (dim == 2) kb_raw_nflags<4><<<grid(BK_RAWN), tp(BK_RAWN), 0, st>>>(dd, bo(BK_RAWN), n, stage);
+        else kb_raw_nflags<3><<<grid(BK_RAWN), tp(BK_RAWN), 0, st>>>(dd, bo(BK_RAWN), n, stage);
+        mark(BK_RAWN, 1);
+        mark(BK_NORMAL, 0);
+        if (dim == 2) kb_normal<4><<<grid(BK_NORMAL), tp(BK_NORMAL), 0, st>>>(dd, bo(BK_NORMAL), n, stage);
+        else kb_normal<3><<<grid(BK_NORMAL), tp(BK_NORMAL), 0, st>>>(dd, bo(BK_NORMAL), n, stage);
+        mark(BK_NORMAL, 1);
+        mark(BK_NAO, 0);
+        if (dim == 2) kb_normal_ao<4><<<grid(BK_NAO), tp(BK_NAO), 0, st>>>(dd, bo(BK_NAO), n, stage);
+        else kb_normal_ao<3><<<grid(BK_NAO), tp(BK_NAO), 0, st>>>(dd, bo(BK_NAO), n, stage);
+        mark(BK_NAO, 1);
+        if (dim == 2) {
+            mark(BK_RAWT, 0);
+            kb_raw_tflags<<<grid(BK_RAWT), tp(BK_RAWT), 0, st>>>(dd, bo(BK_RAWT), n);
+            mark(BK_RAWT, 1);
+            mark(BK_TANG, 0);
+            kb_tang<<<grid(BK_TANG), tp(BK_TANG), 0, st>>>(dd, bo(BK_TANG), n, stage);
+            mark(BK_TANG, 1);
+            mark(BK_TAO, 0);
+            kb_tang_ao<<<grid(BK_TAO), tp(BK_TAO), 0, st>>>(dd, bo(BK_TAO), n, stage);
+            mark(BK_TAO, 1);
         }
+        mark(BK_FLUX, 0);
+        const int tf = tp(BK_FLUX);
+        if (dim == 2) {
+            if (stage == 0) kb_flux<2, 0><<<grid(BK_FLUX), tf, 0, st>>>(dd, bo(BK_FLUX), n);
+            else kb_flux<2, 1><<<grid(BK_FLUX), tf, 0, st>>>(dd, bo(BK_FLUX), n);
+        } else {
+            if (stage == 0) kb_flux<1, 0><<<grid(BK_FLUX), tf, 0, st>>>(dd, bo(BK_FLUX), n);
+            else kb_flux<1, 1><<<grid(BK_FLUX), tf, 0, st>>>(dd, bo(BK_FLUX), n);
+        }
+        mark(BK_FLUX, 1);
         mark(BK_UPD, 0);
-        const int tu = plan.tpb[BK_UPD];
+        const int tu = tp(BK_UPD);
         if (dim == 2) {
             if (stage == 0) kb_update<2, 0><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
             else kb_update<2, 1><<<grid(BK_UPD), tu, 0, st>>>(dd, bo(BK_UPD), n);
