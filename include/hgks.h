@@ -174,9 +174,10 @@ typedef struct hgks_batch hgks_batch;
 #define HGKS_BATCH_AUTOTUNE 2   /* choose the block size of each kernel class on the first steps (see hgks_batch_step) */
 
 /* Group n >= 1 solvers of the same dimension on the current device.  One
- * batched step issues one launch per kernel class (40 per step in 2D) whose
- * blocks cover every solver's interfaces; each block works for exactly one
- * solver with that solver's own arithmetic, so every result is bit-identical
+ * batched step issues one launch per kernel class (26 per step in 2D, the sweep
+ * classes covering both sweeps) whose blocks cover every solver's interfaces;
+ * each block works for exactly one solver (and one sweep) with that solver's own
+ * arithmetic, so every result is bit-identical
  * to stepping the solver alone.  The solvers keep their own state, dt, time and
  * counters; they must stay alive, and must not be stepped on their own, while
  * the batch exists.  stream: cudaStream_t cast to void* for all batched work.
@@ -296,8 +297,8 @@ int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms);
  * HGKS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits; no cudaMalloc, cudaFree or other allocation is made.  A
  * configuration whose buffers do not fit (hgks_footprint_bytes(cfg) greater
- * than HGKS_NOALLOC_SCRATCH_BYTES: square 2D grids above 93 x 93 cells, 1D
- * grids above 37 112 cells) is rejected with HGKS_EINVAL.  The first call on a device
+ * than HGKS_NOALLOC_SCRATCH_BYTES: square 2D grids above 74 x 74 cells, 1D
+ * grids above 37 105 cells) is rejected with HGKS_EINVAL.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that device
  * current); make that first call before any stream capture.  All calls share
  * the one array: calls whose work overlaps on the GPU race and corrupt each

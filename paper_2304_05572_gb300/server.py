@@ -4,11 +4,12 @@ Requests (a configuration, an initial state and an end time) arrive over time.
 The server admits a request as soon as its arrival time has passed and the
 device memory its solver needs (hgks_footprint_bytes) fits in the budget;
 admitted solves keep their state resident on the device and advance together:
-every iteration issues one batched group of S2O4 steps (hgks_batch_step, CUDA
-graph replay) per dimension for all resident solves, the 1D and 2D groups on
-their own streams so that they overlap on the device (the group of the faster
-dimension takes more steps, so that both take about the same device time), and
-newly admitted solves join the ones already running.  A solve retires at its
+every iteration issues one group of S2O4 steps (hgks_batch_step, CUDA graph
+replay) per batch, all batches on their own streams so that they overlap on the
+device: one batch per dimension (optionally the 2D solves spread over a few
+batches, a new solve joining the one with the fewest resident cells); the
+batch whose step is faster takes more steps, so that all take about the same
+device time, and newly admitted solves join the ones already running.  A solve retires at its
 end time, when its state turned non-physical (the scheme has no positivity limiter; the status is
 reported with the result) or when its request is cancelled; its state is
 copied back, its memory freed and its latency (completion minus arrival,
@@ -37,18 +38,40 @@ STATUS_CANCELLED = "cancelled"
 
 
 class GpuBackend:
-    """Solvers on the current CUDA device, advanced by one hgks batch per dimension."""
+    """Solvers on the current CUDA device, advanced by hgks batches: one per dimension for 1D,
+    `groups_2d` for 2D, each batch on its own stream.  A batch is addressed by its key, the
+    dimension or a (dimension, group) pair."""
 
-    def __init__(self, stream=None, autotune: bool = False):
+    def __init__(self, stream=None, autotune: bool = False, groups_2d: int = 1):
         import torch
         self._torch = torch
-        # one stream per dimension: the 1D batch (small, latency-bound launches) overlaps on the
-        # device with the 2D batch; `stream`, if given, serves the 2D solves
-        self.streams = {1: torch.cuda.Stream(), 2: stream if stream is not None else torch.cuda.Stream()}
+        # 1D batches (small, latency-bound launches) overlap on the device with the 2D ones, at a
+        # higher priority, so that their few blocks are dispatched as soon as a slot frees instead
+        # of queueing behind the 2D grids (their solves take many short steps and would otherwise
+        # set the tail).  groups_2d > 1 splits the 2D solves over that many batches on separate
+        # streams, so that the latency-bound kernels of one group overlap the others' work; one
+        # batch measured faster (a 16-request burst of small solves: 69.4 Mcell-stage/s with one
+        # 2D batch, 65.5 with two, 57 with three or four), so it is the default.  `stream`, if
+        # given, serves 2D group 0.
+        self.groups = {1: 1, 2: max(1, int(groups_2d))}
+        self._stream2 = stream
+        self.streams = {}
         self.autotune = autotune
-        self._batches = {}        # dim -> (tuple of handles, Batch)
-        self._events = {}         # dim -> (start, end, nsteps) of the last enqueued group of steps
-        self._ms_per_step = {}    # dim -> device time per batched step of the last group
+        self._batches = {}        # key -> (tuple of handles, Batch)
+        self._events = {}         # key -> (start, end, nsteps) of the last enqueued group of steps
+        self._ms_per_step = {}    # key -> device time per batched step of the last group
+
+    def stream(self, key):
+        """The stream of a batch key (created on first use)."""
+        st = self.streams.get(key)
+        if st is None:
+            dim, group = key if isinstance(key, tuple) else (key, 0)
+            if dim == 2 and group == 0 and self._stream2 is not None:
+                st = self._stream2
+            else:
+                st = self._torch.cuda.Stream(priority=-1 if dim == 1 else 0)
+            self.streams[key] = st
+        return st
 
     def footprint(self, cfg) -> int:
         """Device bytes of a solver of cfg; 0 if the library rejects the configuration."""
@@ -58,47 +81,47 @@ class GpuBackend:
             return 0
 
     def create(self, cfg, W):
-        s = hgks.Solver(cfg, stream=self.streams[int(cfg["dim"])])
+        s = hgks.Solver(cfg, stream=self.stream((int(cfg["dim"]), 0)))
         s.hgks_set_state(np.ascontiguousarray(W))
         return s
 
-    def _batch(self, dim, handles):
-        """The dimension's batch over exactly these solvers: created once, then updated in place
+    def _batch(self, key, handles):
+        """The key's batch over exactly these solvers: created once, then updated in place
         when the resident set changes (no reallocation, graph updated rather than rebuilt)."""
-        key = tuple(handles)
-        cur = self._batches.get(dim)
-        if cur is not None and cur[0] == key:
+        members = tuple(handles)
+        cur = self._batches.get(key)
+        if cur is not None and cur[0] == members:
             return cur[1]
         if cur is not None:
             b = cur[1]
-            b.hgks_batch_update(list(key))
+            b.hgks_batch_update(list(members))
         else:
-            b = hgks.Batch(list(key), stream=self.streams[dim])
-        self._batches[dim] = (key, b)
+            b = hgks.Batch(list(members), stream=self.stream(key))
+        self._batches[key] = (members, b)
         return b
 
-    def step(self, dim, handles, t_ends, nsteps):
+    def step(self, key, handles, t_ends, nsteps):
         """Enqueue nsteps batched steps of the given solvers (no wait), timed by CUDA events."""
-        b = self._batch(dim, handles)
-        st = self.streams[dim]
+        b = self._batch(key, handles)
+        st = self.stream(key)
         e0, e1 = self._torch.cuda.Event(enable_timing=True), self._torch.cuda.Event(enable_timing=True)
         e0.record(st)
         b.hgks_batch_step(t_ends, nsteps=nsteps, graph=True, autotune=self.autotune)
         e1.record(st)
-        self._events[dim] = (e0, e1, nsteps)
+        self._events[key] = (e0, e1, nsteps)
 
-    def sync(self, dim):
-        """Wait for the dimension's batch; (t, status, steps) per solver in step() order."""
-        b = self._batches[dim][1]
+    def sync(self, key):
+        """Wait for the key's batch; (t, status, steps) per solver in step() order."""
+        b = self._batches[key][1]
         b.hgks_batch_sync()
-        ev = self._events.pop(dim, None)
+        ev = self._events.pop(key, None)
         if ev is not None and ev[2] > 0:
-            self._ms_per_step[dim] = ev[0].elapsed_time(ev[1]) / ev[2]
+            self._ms_per_step[key] = ev[0].elapsed_time(ev[1]) / ev[2]
         return list(zip(*b.hgks_batch_status()))
 
-    def ms_per_step(self, dim):
-        """Device time of one batched step of the dimension's last group (None before the first)."""
-        return self._ms_per_step.get(dim)
+    def ms_per_step(self, key):
+        """Device time of one batched step of the key's last group of steps (None before the first)."""
+        return self._ms_per_step.get(key)
 
     def fetch(self, handle):
         return handle.hgks_get_state()
@@ -114,9 +137,9 @@ class GpuBackend:
 
 class Server:
     def __init__(self, budget_bytes: float, stream=None, steps_per_iter: int = 4, autotune: bool = False,
-                 backend=None, clock=time.perf_counter):
+                 backend=None, clock=time.perf_counter, groups_2d: int = 1):
         self.budget = float(budget_bytes)
-        self.backend = backend if backend is not None else GpuBackend(stream, autotune)
+        self.backend = backend if backend is not None else GpuBackend(stream, autotune, groups_2d)
         self.steps_per_iter = int(steps_per_iter)
         self.max_steps_factor = 16
         self.clock = clock
@@ -126,9 +149,24 @@ class Server:
         self.iterations = 0
         self.peak_resident = 0
 
+    def _key(self, req):
+        """The batch a new solve joins: its dimension, or, where the backend splits a dimension
+        over several batches (its `groups`), the (dimension, group) whose resident solves hold
+        the fewest cells.  A solve stays in its batch until it retires."""
+        dim = int(req["cfg"]["dim"])
+        ng = int(getattr(self.backend, "groups", {}).get(dim, 1))
+        if ng <= 1:
+            return dim
+        load = [0] * ng
+        for a in self.active.values():
+            k = a["key"]
+            if isinstance(k, tuple) and k[0] == dim:
+                load[k[1]] += int(np.prod(np.shape(a["req"]["W"])[1:]))
+        return (dim, int(np.argmin(load)))
+
     def _admit(self, req, now):
         h = self.backend.create(req["cfg"], req["W"])
-        self.active[req["id"]] = dict(req=req, handle=h, bytes=req["bytes"], t_admit=now)
+        self.active[req["id"]] = dict(req=req, handle=h, bytes=req["bytes"], t_admit=now, key=self._key(req))
         self.used += req["bytes"]
         self.peak_resident = max(self.peak_resident, len(self.active))
 
@@ -144,12 +182,12 @@ class Server:
         self.used -= a["bytes"]
         self._answer(a["req"], now, status, W=W, t=t, steps=steps, admitted=a["t_admit"])
 
-    def _steps_per_dim(self, by_dim):
-        """Steps of each dimension's group in this iteration: the dimension whose batched step
-        takes longest on the device does steps_per_iter steps, the others as many as fit in the
-        same device time (up to max_steps_factor times more), so that no batch waits idle for
-        the other at the end of an iteration.  Without timings (first iterations, or a backend
-        that reports none) every dimension does steps_per_iter."""
+    def _steps_per_batch(self, by_dim):
+        """Steps of each batch in this iteration: the batch whose step takes longest on the
+        device does steps_per_iter steps, the others as many as fit in the same device time (up
+        to max_steps_factor times more), so that no batch waits idle for another at the end of
+        an iteration.  Without timings (first iterations, or a backend that reports none) every
+        batch does steps_per_iter."""
         ms = {d: getattr(self.backend, "ms_per_step", lambda d: None)(d) for d in by_dim}
         known = [v for v in ms.values() if v]
         if len(by_dim) < 2 or len(known) < len(by_dim):
@@ -199,9 +237,9 @@ class Server:
                 continue
             by_dim = {}
             for rid, a in self.active.items():
-                by_dim.setdefault(int(a["req"]["cfg"]["dim"]), []).append(rid)
-            nsteps = self._steps_per_dim(by_dim)
-            for dim, ids in by_dim.items():             # enqueue every dimension first (they overlap)
+                by_dim.setdefault(a["key"], []).append(rid)
+            nsteps = self._steps_per_batch(by_dim)
+            for dim, ids in by_dim.items():             # enqueue every batch first (they overlap)
                 ids.sort()
                 self.backend.step(dim, [self.active[i]["handle"] for i in ids],
                                   [self.active[i]["req"]["t_end"] for i in ids], nsteps[dim])

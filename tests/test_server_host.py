@@ -158,3 +158,35 @@ def test_faster_dimension_takes_more_steps_per_iteration():
     srv2 = server.Server(budget_bytes=1e9, steps_per_iter=4, backend=be2, clock=be2.clock)
     srv2.run([_req(0, 0.0, 0.2, 0.01, 10, dim=1)])
     assert {n for _, n in be2.requested} == {4}
+
+
+class GroupedBackend(FakeBackend):
+    """FakeBackend that splits the 2D solves over two batches, as the GPU backend does."""
+    groups = {1: 1, 2: 2}
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.members = {}
+
+    def step(self, key, handles, t_ends, nsteps):
+        self.members.setdefault(key, set()).update(id(h) for h in handles)
+        super().step(key, handles, t_ends, nsteps)
+
+
+def test_2d_solves_join_the_least_loaded_batch():
+    clock = FakeClock()
+    be = GroupedBackend(clock)
+    srv = server.Server(budget_bytes=1e9, steps_per_iter=2, backend=be, clock=clock)
+    big = dict(_req(0, 0.0, 1.0, 0.125, 10), W=np.zeros((4, 40, 40)))
+    small = [dict(_req(k, 0.0, 0.5, 0.125, 10), W=np.zeros((4, 10, 10))) for k in (1, 2, 3)]
+    trace = [big] + small + [_req(4, 0.0, 0.25, 0.125, 10, dim=1)]
+    res = srv.run(trace)
+    for r in trace:
+        got = res[r["id"]]
+        assert got["status"] == server.STATUS_OK and got["t"] == r["t_end"]
+        assert got["steps"] == int(np.ceil(r["t_end"] / r["cfg"]["dt"]))
+        assert np.all(got["W"] == got["steps"])
+    # the 40x40 solve holds batch (2, 0) alone; the three 10x10 ones go to (2, 1), the lighter
+    # batch at each admission; the 1D solve keeps its dimension's single batch
+    assert set(be.members) == {(2, 0), (2, 1), 1}
+    assert len(be.members[(2, 0)]) == 1 and len(be.members[(2, 1)]) == 3 and len(be.members[1]) == 1
