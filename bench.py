@@ -77,10 +77,11 @@ ORACLE_FLUX_FLOP_PER_GP = 7025.0
 FLUX_KERNEL_TANG_FLOP_PER_GP = 16 * 9 + 8 * 9 + 2 * 6 + 8
 NONFLUX_FLOP_PER_CELL_STAGE = {"linear": 2721.3, "wenoao": 19486.7, "hybrid": 3525.5,
                                "hybrid_troubled_fraction": 0.004106}
-# DRAM bytes (read + write) per flux launch, ncu at 512^2 (the kernel with the fused tangential
-# reconstruction, second stage: 35.23 MB read + 0.40 MB written, and 35.24 + 0.63 MB), scaled to
-# 1024^2 by the Gauss points per launch (the line buffer it reads is linear in them).
-FLUX_DRAM_BYTES_PER_GP = (35.23e6 + 0.40e6 + 35.24e6 + 0.63e6) / 2 / (2 * 512 * 513)
+# DRAM bytes (read + write) per flux launch (both sweeps), one ncu pass over a whole 1024^2 step
+# with the caches carried from kernel to kernel (--cache-control none), as the step runs: first
+# stage 274.6 MB read + 118.3 MB written, second stage 275.9 + 61.7 MB; per Gauss point of the
+# launch (4 * 1024 * 1025 of them).
+FLUX_DRAM_BYTES_PER_GP = (274.63e6 + 118.26e6 + 275.91e6 + 61.70e6) / 2 / (4 * 1024 * 1025)
 
 
 def algorithmic_flop_per_cell_stage(n, troubled_fraction):
@@ -639,7 +640,7 @@ def main():
     roofline = None
     if flux_calls:
         avg_ms = flux_ms / flux_calls
-        gp_per_launch = 2 * (n + 1) * n          # Gauss points of one sweep
+        gp_per_launch = 2 * 2 * (n + 1) * n      # Gauss points of both sweeps (one launch per stage)
         # the kernel's work per Gauss point: the flux, and on sweeps of 65 536 segments or more the
         # fused reconstruction of the smooth tangential passes
         per_gp = FLUX_ALG_FLOP_PER_GP + (FLUX_KERNEL_TANG_FLOP_PER_GP if n * (n + 1) >= 65536 else 0.0)

@@ -182,8 +182,8 @@ Layout plan(const hgks_config* c, const Params& P, const Sweep* sw)
             L.off_flagT[d] = take((size_t)S.nt * S.nm);
             L.off_itemsT[d] = take((size_t)S.nt * S.nm * 4 * sizeof(uint32_t));
         }
-        int ngp = c->dim == 2 ? 2 : 1;
-        L.off_flux[d] = take((size_t)ngp * 2 * P.g.nv * S.nt * S.nm * sizeof(double));
+        // segment fluxes (the Gauss points already combined): [2 outputs][nv][nt][nn+1]
+        L.off_flux[d] = take((size_t)2 * P.g.nv * S.nt * S.nm * sizeof(double));
     }
     L.total = off;
     return L;

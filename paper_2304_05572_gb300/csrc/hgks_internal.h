@@ -57,7 +57,7 @@ struct Sweep {
     uint8_t* rawT;             // [nt + 4][nm]       raw tangential flag bits, lines -2..nt+1
     uint8_t* flagT;            // [nt][nm]           final tangential flag bits
     double* gp;                // [2][6][nv][nt][nm] Gauss-point states
-    double* flux;              // [ngp][2][nv][nt][nm] per-Gauss-point flux outputs (global order)
+    double* flux;              // [2][nv][nt][nm] segment fluxes (Gauss points combined; global component order)
     uint32_t* itemsN;          // AO work list, normal pass
     uint32_t* itemsT;          // AO work list, tangential passes
     const char* lo;            // the solver's device buffers: [lo, hi) (checked by the debug build)

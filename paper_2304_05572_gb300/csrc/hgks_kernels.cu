@@ -812,17 +812,26 @@ __global__ void k_tang_ao(const SolveDesc* __restrict__ D, int nb0, int stage)
 
 
 // ---------------------------------------------------------------- flux and update
+constexpr int kFluxMaxBlock = 256;          // largest block of a flux launch (solo 64, batched up to 256)
+
 template <int DIM, int STAGE, bool PRFIX>
 __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ctrl, long long id)
 {
-    if (ctrl->done) return;
+    if (ctrl->done) return;                   // the same for every thread of a block
     constexpr int NV = DIM + 2;
-    constexpr int NGP = DIM == 2 ? 2 : 1;
-    long long per = (long long)S.nt * S.nm;
-    long long total = per * NGP;
-    if (id >= total) return;
-    int g = (int)(id / per);
-    long long o = id % per;
+    const long long per = (long long)S.nt * S.nm;
+    // 2D: warps in pairs, warp 2w on Gauss point 0 and warp 2w + 1 on Gauss point 1 of the same
+    // 32 segments, so that the pair shares its stencil reads in cache and sums the segment flux
+    int g = 0;
+    long long o = id;
+    if constexpr (DIM == 2) {
+        const long long warp = id >> 5;
+        g = (int)(warp & 1);
+        o = ((warp >> 1) << 5) + (id & 31);
+    }
+    bool valid = o < per;
+    double o0[NV], o1[NV];
+    if (valid) {
     double Wq[6][NV];
     if constexpr (DIM == 2) {
         if (S.tlanes == 4) {
@@ -871,16 +880,46 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
     fc.Kq = P.K + (double)DIM; fc.cslope = 4.0 / fc.Kq;
     fc.mu = P.mu; fc.c1 = P.c1; fc.c2 = P.c2; fc.viscous = P.viscous; fc.tau_zero = P.tau_zero;
     fc.prfix = P.prfix;
-    double o0[NV], o1[NV];
-    bool ok = gks_flux<DIM, STAGE, PRFIX>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1);
-    if (!ok) { ctrl->status = HGKS_ENONPHYSICAL; return; }
+    if (!gks_flux<DIM, STAGE, PRFIX>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1)) {
+        ctrl->status = HGKS_ENONPHYSICAL;
+        valid = false;
+    }
+    }
+    // the segment flux (Gauss weights 1/2): the Gauss point 1 warp hands its fluxes to its partner
+    // through shared memory; stored per segment as [output][component][segment]
+    constexpr int NO = STAGE == 0 ? 2 : 1;
+    if constexpr (DIM == 2) {
+        __shared__ double pair[kFluxMaxBlock / 2][2 * 4];
+        const int slot = ((threadIdx.x >> 6) << 5) + (threadIdx.x & 31);
+        if (g == 1 && valid) {
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                pair[slot][k] = o0[k];
+                if (STAGE == 0) pair[slot][NV + k] = o1[k];
+            }
+        }
+        __syncthreads();
+        if (g == 1 || !valid) return;
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            o0[k] = fma(0.5, o0[k], 0.5 * pair[slot][k]);
+            if (STAGE == 0) o1[k] = fma(0.5, o1[k], 0.5 * pair[slot][NV + k]);
+        }
+    } else {
+        if (!valid) return;
+    }
 #pragma unroll
     for (int k = 0; k < NV; k++) {
-        int gk = S.perm[k];
-        stc(S.flux + (long long)((g * 2 + 0) * NV + gk) * per + o, o0[k], S);
-        if (STAGE == 0) stc(S.flux + (long long)((g * 2 + 1) * NV + gk) * per + o, o1[k], S);
+        const int gk = S.perm[k];
+        stc(S.flux + (long long)(0 * NV + gk) * per + o, o0[k], S);
+        if (NO == 2) stc(S.flux + (long long)(1 * NV + gk) * per + o, o1[k], S);
     }
 }
+
+// Threads of a 2D flux launch for a sweep of `per` segments: two Gauss points per segment, the
+// segments padded to whole warps (see b_flux).
+inline long long flux_threads(int dim, long long per) { return dim == 2 ? 2 * ((per + 31) / 32) * 32 : per; }
+
 
 template <int DIM, int STAGE, bool PRFIX>
 __device__ __noinline__ void flux_nl(const SolveDesc& d, int dir, long long id)
@@ -918,18 +957,16 @@ __device__ __forceinline__ void b_update(const Params& P, const Sweep& Sx, const
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         double fx0[2], fx1[2], fy0[2] = {0, 0}, fy1[2] = {0, 0};
+        // segment fluxes [output][component][segment] of the interfaces on either side
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             const double* fb = Sx.flux;
+            fx0[s] = ldc(fb + (long long)(0 * NV + k) * perx + ox + s, g);
+            fx1[s] = STAGE == 0 ? ldc(fb + (long long)(1 * NV + k) * perx + ox + s, g) : 0.0;
             if constexpr (DIM == 2) {
-                fx0[s] = fma(0.5, ldc(fb + (long long)((0 * 2 + 0) * NV + k) * perx + ox + s, g), 0.5 * ldc(fb + (long long)((1 * 2 + 0) * NV + k) * perx + ox + s, g));
-                fx1[s] = STAGE == 0 ? fma(0.5, ldc(fb + (long long)((0 * 2 + 1) * NV + k) * perx + ox + s, g), 0.5 * ldc(fb + (long long)((1 * 2 + 1) * NV + k) * perx + ox + s, g)) : 0.0;
                 const double* gb = Sy.flux;
-                fy0[s] = fma(0.5, ldc(gb + (long long)((0 * 2 + 0) * NV + k) * pery + oy + s, g), 0.5 * ldc(gb + (long long)((1 * 2 + 0) * NV + k) * pery + oy + s, g));
-                fy1[s] = STAGE == 0 ? fma(0.5, ldc(gb + (long long)((0 * 2 + 1) * NV + k) * pery + oy + s, g), 0.5 * ldc(gb + (long long)((1 * 2 + 1) * NV + k) * pery + oy + s, g)) : 0.0;
-            } else {
-                fx0[s] = ldc(fb + (long long)(0 * NV + k) * perx + ox + s, g);
-                fx1[s] = STAGE == 0 ? ldc(fb + (long long)(1 * NV + k) * perx + ox + s, g) : 0.0;
+                fy0[s] = ldc(gb + (long long)(0 * NV + k) * pery + oy + s, g);
+                fy1[s] = STAGE == 0 ? ldc(gb + (long long)(1 * NV + k) * pery + oy + s, g) : 0.0;
             }
         }
         if (STAGE == 0) {
@@ -1229,7 +1266,7 @@ static void enqueue_sweeps(hgks_solver* s, int stage)
         }
     }
     timed(s, KC_FLUX, 1, [&] {
-        unsigned int g = pair([](const Sweep& S) { return blocks_for((long long)S.nt * S.nm * (DIM == 2 ? 2 : 1), 64); }, nb);
+        unsigned int g = pair([](const Sweep& S) { return blocks_for(flux_threads(DIM, (long long)S.nt * S.nm), 64); }, nb);
         const int n0 = (int)nb[0];
         if (P.prfix != 0.0) {
             if (stage == 0) k_flux<DIM, 0, true><<<g, 64, 0, st>>>(D, n0);
@@ -1330,7 +1367,7 @@ static long long batch_unit_blocks(const SolveDesc& d, int dim, int c, int dir, 
         case BK_RAWT: if (dim != 2) return 0; b = blocks_for((long long)(S.nt + 2) * S.nm * S.tlanes, t); break;
         case BK_TANG: if (dim != 2) return 0; b = blocks_for((long long)S.nt * S.nm * S.tlanes, t); break;
         case BK_TAO: if (dim != 2) return 0; b = blocks_for((long long)S.nt * S.nm * 4 * 4, t * 8); break;
-        case BK_FLUX: b = blocks_for((long long)S.nt * S.nm * (dim == 2 ? 2 : 1), t); break;
+        case BK_FLUX: b = blocks_for(flux_threads(dim, (long long)S.nt * S.nm), t); break;
         case BK_UPD: b = blocks_for(cells, t); break;
     }
     return b < 1 ? 1 : b;
