@@ -829,7 +829,7 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
         g = (int)(warp & 1);
         o = ((warp >> 1) << 5) + (id & 31);
     }
-    bool valid = o < per;
+    const bool valid = o < per;
     double o0[NV], o1[NV];
     if (valid) {
     double Wq[6][NV];
@@ -881,8 +881,12 @@ __device__ __forceinline__ void b_flux(const Params& P, const Sweep& S, Ctrl* ct
     fc.mu = P.mu; fc.c1 = P.c1; fc.c2 = P.c2; fc.viscous = P.viscous; fc.tau_zero = P.tau_zero;
     fc.prfix = P.prfix;
     if (!gks_flux<DIM, STAGE, PRFIX>(fc, Wq[0], Wq[1], Wq[2], Wq[3], Wq[4], Wq[5], ctrl->dt, o0, o1)) {
+        // a non-physical state: the status is latched and the flux is a NaN, so that what the
+        // failed step leaves behind does not depend on anything but the solve itself
         ctrl->status = HGKS_ENONPHYSICAL;
-        valid = false;
+        const double nan = __longlong_as_double(0x7FF8000000000000LL);
+#pragma unroll
+        for (int k = 0; k < NV; k++) { o0[k] = nan; o1[k] = nan; }
     }
     }
     // the segment flux (Gauss weights 1/2): the Gauss point 1 warp hands its fluxes to its partner

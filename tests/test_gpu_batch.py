@@ -111,7 +111,9 @@ def test_failed_solver_stops_alone_and_others_continue():
     import torch
     bad = P.riemann4_2d(32, seed=P.BATCH_SEED + 1 + 3)[:2]
     good = [P.riemann4_2d(n, seed=P.BATCH_SEED + 1 + k)[:2] for k, n in ((0, 24), (1, 40))]
-    cases = [good[0], bad, good[1]]
+    # the other two seeds of the batched set that break (at steps 6 and 7)
+    bad2 = [P.riemann4_2d(n, seed=P.BATCH_SEED + 1 + k)[:2] for k, n in ((214, 40), (224, 48))]
+    cases = [good[0], bad, good[1]] + bad2
     stream = torch.cuda.Stream()
     solvers = []
     for cfg, W in cases:
@@ -119,9 +121,9 @@ def test_failed_solver_stops_alone_and_others_continue():
         s.hgks_set_state(np.ascontiguousarray(W))
         solvers.append(s)
     b = hgks.Batch(solvers, stream=stream)
-    b.hgks_batch_step([1e9] * 3, nsteps=12, graph=True)
+    b.hgks_batch_step([1e9] * len(cases), nsteps=12, graph=True)
     active, failed = b.hgks_batch_sync()
-    assert failed == 1 and active == 2
+    assert failed == 3 and active == 2
     ts, sts, ns = b.hgks_batch_status()
     for s, t, st, n in zip(solvers, ts, sts, ns):
         ref = s.hgks_get_stats()
