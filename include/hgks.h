@@ -125,7 +125,9 @@ int hgks_set_state(hgks_solver* s, const double* W, int on_device, double t0);
  * waits for the stream and stores the number of steps actually taken; with
  * steps_done == NULL it returns after enqueueing (errors latched on the device
  * surface at the next waiting call).  Returns HGKS_ENONPHYSICAL if a
- * non-physical state was detected (the solver then stops advancing). */
+ * non-physical state was detected (the solver then stops advancing; the state
+ * the failing step leaves holds NaN wherever a Gauss-point flux met a
+ * non-physical state, the same bits however the solver was stepped). */
 int hgks_step(hgks_solver* s, double t_end, int max_steps, int* steps_done);
 
 /* Copy the state out ([nv][ny][nx], FP64) to host (on_device = 0) or device (1)

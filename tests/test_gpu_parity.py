@@ -66,8 +66,10 @@ def check_step(cfg, W, label="", t0=0.0):
     Wo, dt, fo, mo = oracle.step_flags(cfg, W, margins=True, wstar=Wstar, t0=t0)
     assert st["last_dt"] == dt, (label, st["last_dt"], dt)
     assert set(fg) == set(fo)
+    check_step.flips = {}
     for key in fo:
         diff = fg[key] != fo[key]
+        check_step.flips[key] = (int(diff.sum()), int(diff.size))
         if key[0] == 0:
             assert int(diff.sum()) == 0, (label, key, int(diff.sum()))
         else:
@@ -247,12 +249,16 @@ def test_riemann4_1024_full_size_step():
     against the oracle."""
     cfg, W, _ = P.riemann4_2d(1024)
     check_step(cfg, W, "1024^2")
+    print("1024^2 step 1: flags differing from the oracle's (stage, sweep, kind): (count, decisions)",
+          check_step.flips)
     s = hgks.Solver(cfg)
     s.hgks_set_state(W)
     assert s.hgks_step(1e9, 10) == 10
     W10, t10 = s.hgks_get_state(), s.hgks_get_time()
     s.hgks_destroy_solver()
     check_step(cfg, W10, "1024^2 step 11", t0=t10)
+    print("1024^2 step 11: flags differing from the oracle's (stage, sweep, kind): (count, decisions)",
+          check_step.flips)
 
 
 # ------------------------------------------------------------------ API behaviour
