@@ -58,6 +58,8 @@ def lib():
             L.or_linear_face.argtypes = [_DP, ctypes.c_double, ctypes.c_int, _DP, _DP]
             L.or_indicator.argtypes = [_DP, ctypes.c_double]
             L.opc_read.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+            L.or_gauss_scalar.argtypes = [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          _DP, _DP]
             _lib = L
     return _lib
 
@@ -104,6 +106,16 @@ def count_linear_face(q5, h: float, side: int) -> dict:
     v, d = ctypes.c_double(), ctypes.c_double()
     lib().opc_reset()
     lib().or_linear_face(_dp(_arr(q5)), 1.0 / (12.0 * h), int(side), ctypes.byref(v), ctypes.byref(d))
+    return _read()
+
+
+def count_gauss_scalar(q5, use_ao: bool = False) -> dict:
+    """Operations of one oracle Gauss-point reconstruction of a 5-cell window (values and
+    cell-unit derivatives at both Gauss points; linear, or WENO-AO with use_ao)."""
+    from . import _dp, _arr
+    v, d = np.zeros(2), np.zeros(2)
+    lib().opc_reset()
+    lib().or_gauss_scalar(_dp(_arr(q5)), int(use_ao), 0.85, 0.85, 1e-8, _dp(v), _dp(d))
     return _read()
 
 

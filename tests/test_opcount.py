@@ -72,3 +72,20 @@ def test_closed_form_flux_count():
     assert closed < lit / 3
     # tau = 0 drops every non-equilibrium term; the Prandtl fix adds the heat-flux moments
     assert cnt["2d_tau0_stage1"]["flop"] < closed < cnt["2d_ns_prfix_stage1"]["flop"]
+
+
+def test_fused_gauss_point_reconstruction_count():
+    """The flux kernel's share of the tangential reconstruction (the smooth passes at its own
+    Gauss point) enters the flux roofline with the closed-form count 236: 24 quartic
+    evaluations (16 values: 4 passes x 4 components; 8 derivatives: the Q^l, Q^r passes) of
+    one multiply and four fma each (9 operations), 2 positivity tests (rho E - |m|^2/2 > 0:
+    m_y^2, fma for m_x^2 + m_y^2, the half, rho E and the difference: 6) and 8 derivative
+    scalings.  The oracle evaluates the same quartics from the printed formulas at
+    more than twice that (its count of one window's 2 values and 2 derivatives), so, as for
+    the flux, the closed form is the lower figure; the whole-step numerator takes this part
+    from the oracle's count of the reconstruction and not from the flux kernel's."""
+    import bench
+    per_quartic = 1 + 2 * 4
+    assert bench.FLUX_KERNEL_TANG_FLOP_PER_GP == (16 + 8) * per_quartic + 2 * 6 + 8 == 236
+    c = opcount.count_gauss_scalar([1.0, 2.0, 3.5, 2.0, 1.5])
+    assert opcount.flop(c) / 4 > 2 * per_quartic
