@@ -395,11 +395,11 @@ __global__ void k_normal(const SolveDesc* __restrict__ D, int nb0, int stage)
 // Troubled items of one compacted WENO-AO pass at or above which every item gets one lane, below
 // which an aligned group of 4 lanes (one characteristic field per lane).  The lane-group form
 // repeats the eigenvector work in each of its lanes (about 1.9 times the FP64 instructions per
-// item) and pays only while the items leave the schedulers short of warps: below ~10^4 items the
-// one-lane chain of a few thousand FP64 instructions sets the pass's duration, above it the
-// one-lane form's lower instruction count does.  A constant, not a function of the launch, so
-// that a solve takes the same form in its own kernels and in batched ones.
-constexpr unsigned int kAoOneLaneMin = 8192;
+// item) and pays only while the items leave the schedulers short of warps; measured on this part
+// (512^2 and 1024^2 four-quadrant steps, 200x100 tube, thresholds 8192 / 32768 / 131072) the
+// crossover lies near 32768 items.  A constant, not a function of the launch, so that a solve
+// takes the same form in its own kernels and in batched ones.
+constexpr unsigned int kAoOneLaneMin = 32768;
 
 // The window (cells i-2..i+2 across the face, all components) and the face average of the
 // troubled side `it` of the normal pass.

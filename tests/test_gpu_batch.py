@@ -25,9 +25,9 @@ def _cases_2d():
     out.append((cfg, W))
     cfg, W, _ = P.viscous_shock_tube(40, 20, Re=300.0)
     out.append((cfg, W))
-    # WENO-AO everywhere at 72x64: every compacted pass holds 9344 to 18688 items, above the size
-    # from which the passes give each item one lane (the others here use lane groups)
-    cfg, W, _ = P.random_smooth_2d(72, 64)
+    # WENO-AO everywhere at 128x128: every compacted pass holds 34572 to 66048 items, above the
+    # size from which the passes give each item one lane (the others here use lane groups)
+    cfg, W, _ = P.random_smooth_2d(128, 128)
     out.append((dict(cfg, recon_mode="wenoao"), W))
     return out
 
@@ -74,8 +74,8 @@ def test_batch_2d_bitwise_equal_to_alone(graph, autotune):
 def test_batch_1d_and_continuation():
     import torch
     cases = [P.sod_1d(n)[:2] for n in (50, 200, 333)] + [P.blast_1d(120)[:2]]
-    # WENO-AO everywhere on 5000 cells: 10002 troubled sides per pass, one lane each
-    cfg, W, _ = P.sod_1d(5000)
+    # WENO-AO everywhere on 20000 cells: 40002 troubled sides per pass, one lane each
+    cfg, W, _ = P.sod_1d(20000)
     cases.append((dict(cfg, recon_mode="wenoao"), W))
     stream = torch.cuda.Stream()
     solvers = []

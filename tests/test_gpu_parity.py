@@ -164,10 +164,10 @@ def test_recon_modes_2d(mode):
     check_step(cfg, W, mode)
 
 
-@pytest.mark.parametrize("nx,ny", [(24, 20), (72, 64)])
+@pytest.mark.parametrize("nx,ny", [(24, 20), (128, 128)])
 def test_wenoao_passes_in_both_lane_forms(nx, ny):
-    """WENO-AO everywhere: at 24x20 every compacted pass holds fewer than 8192 items and runs
-    one item per group of 4 lanes; at 72x64 every pass holds 9344 to 18688 items and runs one
+    """WENO-AO everywhere: at 24x20 every compacted pass holds fewer than 32768 items and runs
+    one item per group of 4 lanes; at 128x128 every pass holds 34572 to 66048 items and runs one
     item per lane.  Both match the oracle step by step."""
     cfg, W, _ = P.random_smooth_2d(nx, ny)
     cfg["recon_mode"] = "wenoao"
