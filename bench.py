@@ -59,7 +59,9 @@ WORKLOAD = "four-quadrant 2D Riemann problem, 1024^2 cells, hybrid WENO-AO HGKS,
 # two), kept fixed here so that the yardstick does not move when a kernel changes:
 # * the flux per Gauss point: the closed form of the flux kernel (2D Euler, tau > 0), counted on
 #   the host by paper_2304_05572_gb300/flopcount.py: 1433 operations in the first stage (F(dt/2)
-#   and the F^n + dt/6 dF^n combination), 1389 in the second;
+#   and the F^n + dt/6 dF^n combination), 1389 in the second; on sweeps of 65 536 segments or
+#   more the kernel also reconstructs its Gauss point's smooth tangential passes
+#   (FLUX_KERNEL_TANG_FLOP_PER_GP); one launch covers both sweeps of a stage;
 # * the rest of the step per cell-stage (indicator, reconstruction, update, time step), counted on
 #   the oracle by oracle/opcount.py on the first step of the 1024^2 problem (the oracle evaluates
 #   these formulas as the paper prints them): every cell smooth 2721.3, every cell troubled
