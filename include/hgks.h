@@ -176,7 +176,7 @@ typedef struct hgks_batch hgks_batch;
 #define HGKS_BATCH_AUTOTUNE 2   /* choose the block size of each kernel class on the first steps (see hgks_batch_step) */
 
 /* Group n >= 1 solvers of the same dimension on the current device.  One
- * batched step issues one launch per kernel class (26 per step in 2D, the sweep
+ * batched step issues one launch per kernel class (24 per step in 2D, the sweep
  * classes covering both sweeps) whose blocks cover every solver's interfaces;
  * each block works for exactly one solver (and one sweep) with that solver's own
  * arithmetic, so every result is bit-identical

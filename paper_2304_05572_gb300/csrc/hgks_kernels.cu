@@ -76,9 +76,12 @@ __device__ __forceinline__ double cell_centre(double origin, int i, double h)
     return (ex(origin) + (ex((double)i) + ex(0.5)) * ex(h)).v;
 }
 
-__device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ W, const Ctrl* __restrict__ ctrl, long long id)
+// The first thread of a stage's x-ghost launch also empties the stage's work lists (no kernel
+// of the stage reads them before the ghost fills are complete).
+__device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ W, Ctrl* __restrict__ ctrl, long long id)
 {
     if (ctrl->done) return;
+    if (id == 0) ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
     const GridGeom& g = P.g;
     int rowsI = g.dim == 2 ? g.ny : 1;
     long long total = (long long)g.nv * rowsI * NG * 2;
@@ -104,7 +107,7 @@ __device__ __forceinline__ void b_ghost_x(const Params& P, double* __restrict__ 
     stc(base + dst, v, g);
 }
 
-__global__ void k_ghost_x(Params P, double* __restrict__ W, const Ctrl* __restrict__ ctrl)
+__global__ void k_ghost_x(Params P, double* __restrict__ W, Ctrl* __restrict__ ctrl)
 {
     b_ghost_x(P, W, ctrl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
@@ -162,10 +165,6 @@ __global__ void k_begin_step(Ctrl* ctrl)
     ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
 }
 
-__global__ void k_begin_stage(Ctrl* ctrl)
-{
-    ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
-}
 
 // Sec. 3 preamble: dt = CFL min(h/(|U|+a), h^2/(4 nu)), h = min(dx, dy), nu = mu/rho;
 // same evaluation order as the CPU reference so that dt is reproduced exactly.
@@ -1055,8 +1054,6 @@ __global__ void kb_ctrl(const SolveDesc* __restrict__ D, int n, int what, const 
         if (!done && !(dt > 0.0 && dt < 1e300)) { ctrl->status = HGKS_ENONPHYSICAL; done = 1; }
         ctrl->dt = dt;
         ctrl->done = done;
-    } else if (what == 2) {                // begin stage
-        ctrl->cnt[0][0] = ctrl->cnt[0][1] = ctrl->cnt[1][0] = ctrl->cnt[1][1] = 0;
     } else {                               // end step
         if (ctrl->done) return;
         ctrl->t += ctrl->dt;
@@ -1289,7 +1286,6 @@ static void enqueue_stage(hgks_solver* s, int stage)
     const Params& P = s->P;
     cudaStream_t st = s->stream;
     double* Win = stage == 0 ? s->W : s->Ws;
-    timed(s, KC_MISC, 1, [&] { k_begin_stage<<<1, 1, 0, st>>>(s->ctrl); });
     timed(s, KC_GHOST, DIM == 2 ? 2 : 1, [&] {
         int rowsI = DIM == 2 ? P.g.ny : 1;
         k_ghost_x<<<blocks_for((long long)P.g.nv * rowsI * NG * 2, TPB), TPB, 0, st>>>(P, Win, s->ctrl);
@@ -1417,7 +1413,6 @@ cudaError_t batch_enqueue_step(const BatchPlan& plan, const SolveDesc* dd, const
     mark(BK_DT, 1);
     kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 1, dtend);
     for (int stage = 0; stage < 2; stage++) {
-        kb_ctrl<<<grid(BK_CTRL), tc, 0, st>>>(dd, n, 2, dtend);
         mark(BK_GHX, 0);
         kb_ghost<<<grid(BK_GHX), tp(BK_GHX), 0, st>>>(dd, bo(BK_GHX), n, stage, 0);
         mark(BK_GHX, 1);
