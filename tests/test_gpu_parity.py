@@ -490,3 +490,25 @@ def test_full_size_diagonal_symmetry_and_conservation():
     Wq, _, _ = hgks.run(cfg_p, Wp, 1.0, max_steps=5)
     tot0, tot1 = Wp.reshape(4, -1).sum(axis=1), Wq.reshape(4, -1).sum(axis=1)
     assert np.all(np.abs(tot1 - tot0) <= 1e-12 * np.abs(Wp).reshape(4, -1).sum(axis=1))
+
+
+def test_largest_grid_properties():
+    """8192^2 (87.5 GB of device memory, work-list entries up to 2^28, flux launches of 2^27
+    threads): symmetric quadrant data stay symmetric under x <-> y with u <-> v over 2 steps,
+    and on a periodic domain the totals stay fixed over one step."""
+    n = 8192
+    st = [(1.0, 0.2, 0.2, 1.0), (0.5, 0.1, -0.3, 0.6), (0.8, -0.4, -0.4, 0.9), (0.5, -0.3, 0.1, 0.6)]
+    cfg = P.base_config(2, n, n, 0, 1, 0, 1, c1=0.01, c2=1.0, bc=["extrap"] * 4)
+    assert hgks.hgks_footprint_bytes(cfg) > 80e9
+    W = P._quadrants(n, n, st)
+    Wg, _, steps = hgks.run(cfg, W, 1.0, max_steps=2)
+    assert steps == 2
+    scale = np.abs(Wg).reshape(4, -1).max(axis=1)
+    assert np.abs(Wg[0] - Wg[0].T).max() <= 1e-12 * scale[0]
+    assert np.abs(Wg[1] - Wg[2].T).max() <= 1e-12 * max(scale[1], scale[2])
+    assert np.abs(Wg[3] - Wg[3].T).max() <= 1e-12 * scale[3]
+    del W, Wg
+    cfg_p, Wp, _ = P.random_smooth_2d(n, n, seed=11, amp=0.2)
+    Wq, _, _ = hgks.run(cfg_p, Wp, 1.0, max_steps=1)
+    tot0, tot1 = Wp.reshape(4, -1).sum(axis=1), Wq.reshape(4, -1).sum(axis=1)
+    assert np.all(np.abs(tot1 - tot0) <= 1e-11 * np.abs(Wp).reshape(4, -1).sum(axis=1))
