@@ -104,6 +104,15 @@ def test_sod_1d_steps_along_the_run():
     check_step(cfg, W2, "sod t=0.15")
 
 
+@pytest.mark.parametrize("n", [4, 5, 7])
+def test_smallest_1d_grids(n):
+    """The smallest grids the library accepts (4 cells, the ghost depth) and ragged ones just
+    above: every stencil reaches into the ghost layers."""
+    cfg, W, _ = P.sod_1d(n)
+    for k in range(3):
+        W, _, _, _ = check_step(cfg, W, "sod %d step %d" % (n, k))
+
+
 def test_sod_1d_full_run_close_to_oracle():
     cfg, W, t_end = P.sod_1d(200)
     Wg, tg, ng = hgks.run(cfg, W, t_end)
@@ -143,7 +152,7 @@ def test_blast_1d_positivity_path():
 
 # ------------------------------------------------------------------ 2D
 
-@pytest.mark.parametrize("nx,ny", [(37, 29), (64, 48)])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (64, 48), (4, 4), (5, 9), (4, 33)])
 def test_riemann4_steps(nx, ny):
     cfg, W, _ = P.riemann4_2d(nx, ny=ny)
     for n in range(3):
