@@ -264,6 +264,15 @@ int hgks_debug_bounds(unsigned long long* count, unsigned long long* first_addre
  * HGKS_ECUDA (message in hgks_last_error(NULL)). */
 int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms);
 
+/* Check of the flux's reciprocal (a measurement helper like the probe above; the
+ * paper has no counterpart).  The flux forms 1/x as the hardware's approximate
+ * reciprocal refined by two Newton-Raphson steps instead of a division; this
+ * evaluates it on n >= 1 arguments spread log-uniformly over 1e-8..1e8 with both
+ * signs on the current device (default stream; the call waits) and stores in
+ * *max_ulp the largest distance, in units in the last place, from the correctly
+ * rounded IEEE quotient.  Errors: HGKS_EINVAL (n < 1, max_ulp NULL), HGKS_ECUDA. */
+int hgks_check_reciprocal(long long n, unsigned long long* max_ulp);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free single step.                                              */
 /* ------------------------------------------------------------------------ */

@@ -821,6 +821,17 @@ extern "C" int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sm
     return HGKS_OK;
 }
 
+extern "C" int hgks_check_reciprocal(long long n, unsigned long long* max_ulp)
+{
+    if (n < 1 || !max_ulp) return HGKS_EINVAL;
+    cudaError_t e = rcp_check(n, max_ulp);
+    if (e != cudaSuccess) {
+        set_err(g_create_err, "hgks_check_reciprocal: %s", cudaGetErrorString(e));
+        return HGKS_ECUDA;
+    }
+    return HGKS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free single step (hgks_step_noalloc): the same S2O4 step as a solver
 // performs, with every intermediate buffer carved out of one file-scope device

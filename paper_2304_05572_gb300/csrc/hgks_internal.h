@@ -150,6 +150,7 @@ int device_sm_count();
 int debug_bounds_read(unsigned long long* count, unsigned long long* first);
 // FP64 rate probe: `blocks` blocks of 256 threads, 8 DFMA chains of `iters` steps per thread
 cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters);
+cudaError_t rcp_check(long long n, unsigned long long* max_ulp);
 
 // batched execution (hgks_kernels.cu)
 void batch_fill_desc(const hgks_solver* s, SolveDesc& d);

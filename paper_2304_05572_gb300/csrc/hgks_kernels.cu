@@ -1161,6 +1161,40 @@ cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- reciprocal check
+// The flux's Newton-refined reciprocal (rcp_nr) against IEEE division on n arguments spread
+// log-uniformly over 1e-8..1e8 with both signs (splitmix64 hashes of the index); the largest
+// difference in units in the last place goes to g_rcp_max_ulp.
+__device__ unsigned long long g_rcp_max_ulp;
+
+__global__ void k_rcp_check(long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);      // [0, 1)
+    double x = exp10(16.0 * u - 8.0);
+    if (z & 1) x = -x;
+    const double a = rcp_nr(x), b = 1.0 / x;
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const unsigned long long d = (unsigned long long)(ia > ib ? ia - ib : ib - ia);
+    atomicMax(&g_rcp_max_ulp, d);
+}
+
+cudaError_t rcp_check(long long n, unsigned long long* max_ulp)
+{
+    const unsigned long long zero = 0;
+    cudaError_t e = cudaMemcpyToSymbol(g_rcp_max_ulp, &zero, sizeof(zero));
+    if (e != cudaSuccess) return e;
+    k_rcp_check<<<(unsigned)((n + 255) / 256), 256>>>(n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyFromSymbol(max_ulp, g_rcp_max_ulp, sizeof(*max_ulp));
+}
+
 int debug_bounds_read(unsigned long long* count, unsigned long long* first)
 {
 #ifdef HGKS_DEBUG_BOUNDS

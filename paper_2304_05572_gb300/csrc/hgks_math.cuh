@@ -518,18 +518,37 @@ HGKS_HD __forceinline__ double dotv(const double* a, const double* b)
     return s;
 }
 
+// 1/x in the flux's free-order arithmetic: the hardware's approximate reciprocal refined by two
+// Newton-Raphson steps for 1/x, r <- r + r (1 - x r), each of which squares the relative error;
+// within 1 ulp of the correctly rounded quotient for the normal x the flux meets (checked against
+// IEEE division by hgks_check_reciprocal).  A zero x gives a NaN, which the flux's physical-state
+// tests reject as they rejected the infinity of 1/0.  The host build divides.
+HGKS_HD __forceinline__ double rcp_nr(double x)
+{
+#ifdef __CUDA_ARCH__
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+#else
+    return 1.0 / x;
+#endif
+}
+
 template <int DIM>
 HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MState<DIM>& s)
 {
     s.rho = W[0];
-    s.ri = 1.0 / s.rho;
+    s.ri = rcp_nr(s.rho);
     s.U = W[1] * s.ri;
     s.V = DIM == 2 ? W[2] * s.ri : 0.0;
     s.E = W[DIM + 1];
     double mu2 = DIM == 2 ? fma(W[1], s.U, W[2] * s.V) : W[1] * s.U;
     s.p = fc.gm1 * fma(-0.5, mu2, s.E);
     s.h = s.p * s.ri;
-    s.lam = 0.5 / s.h;
+    s.lam = 0.5 * rcp_nr(s.h);
     s.q = fma(s.U, s.U, fma(s.V, s.V, fc.Kq * s.h));
     s.two_lam = 2.0 * s.lam * s.ri;
     s.lam2c = s.lam * fc.cslope * (0.5 * s.two_lam);
@@ -920,10 +939,10 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
     jac_x<DIM>(sc, Wct, fc.gm1, M3);
 
     // collision time (Sec. 3 preamble)
-    const double jump = fabs((sl.p - sr.p) / (sl.p + sr.p));
+    const double jump = fabs((sl.p - sr.p) * rcp_nr(sl.p + sr.p));
     double tau;
     if (fc.tau_zero) tau = 0.0;
-    else if (fc.viscous) tau = fma(fc.c2 * jump, dt, fc.mu / sc.p);
+    else if (fc.viscous) tau = fma(fc.c2 * jump, dt, fc.mu * rcp_nr(sc.p));
     else tau = fma(fc.c2, jump, fc.c1) * dt;
 
     // time integrals of the factors of Eq. (10) over [0, d], d = dt and dt/2
@@ -932,7 +951,7 @@ HGKS_HD __forceinline__ bool gks_flux(const FluxConst& fc, const double* Wl, con
         Cd[0] = dt; Cd[1] = 0.0; Cd[2] = 0.5 * dt * dt; Cd[3] = 0.0; Cd[4] = 0.0; Cd[5] = 0.0;
         Ch[0] = 0.5 * dt; Ch[1] = 0.0; Ch[2] = 0.125 * dt * dt; Ch[3] = 0.0; Ch[4] = 0.0; Ch[5] = 0.0;
     } else {
-        const double eh = exp(-0.5 * dt / tau);
+        const double eh = exp(-0.5 * dt * rcp_nr(tau));
         const double ed = eh * eh;
         const double tt = tau * tau;
 #pragma unroll

@@ -38,7 +38,7 @@ EXPORTED = [
     "hgks_batch_create", "hgks_batch_update", "hgks_batch_step", "hgks_batch_sync", "hgks_batch_status",
     "hgks_batch_info",
     "hgks_batch_last_error",
-    "hgks_batch_destroy", "hgks_debug_bounds", "hgks_probe_fp64", "hgks_step_noalloc",
+    "hgks_batch_destroy", "hgks_debug_bounds", "hgks_probe_fp64", "hgks_check_reciprocal", "hgks_step_noalloc",
 ]
 HGKS_BATCH_GRAPH = 1
 HGKS_BATCH_AUTOTUNE = 2
@@ -118,6 +118,7 @@ def lib():
         L.hgks_batch_destroy.argtypes = [vp]
         L.hgks_batch_destroy.restype = None
         L.hgks_probe_fp64.argtypes = [vp, dp, dp, ip]
+        L.hgks_check_reciprocal.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]
         L.hgks_debug_bounds.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
         L.hgks_step_noalloc.argtypes = [ctypes.POINTER(hgks_config), vp, vp, vp, vp]
         _lib = L
@@ -360,6 +361,16 @@ def hgks_debug_bounds():
     if rc < 0:
         raise HGKSError(rc, lib().hgks_last_error(None).decode())
     return bool(rc), n.value, a.value
+
+
+def hgks_check_reciprocal(n: int = 1 << 24) -> int:
+    """Largest distance in ulps of the flux's Newton-refined reciprocal from IEEE division
+    over n arguments (see include/hgks.h)."""
+    u = ctypes.c_ulonglong(0)
+    rc = lib().hgks_check_reciprocal(int(n), ctypes.byref(u))
+    if rc != HGKS_OK:
+        raise HGKSError(rc, lib().hgks_last_error(None).decode())
+    return u.value
 
 
 def hgks_probe_fp64(stream=None):
