@@ -264,13 +264,16 @@ int hgks_debug_bounds(unsigned long long* count, unsigned long long* first_addre
  * HGKS_ECUDA (message in hgks_last_error(NULL)). */
 int hgks_probe_fp64(void* stream, double* tflops, double* ms, int* sms);
 
-/* Check of the flux's reciprocal (a measurement helper like the probe above; the
- * paper has no counterpart).  The flux forms 1/x as the hardware's approximate
- * reciprocal refined by two Newton-Raphson steps instead of a division; this
- * evaluates it on n >= 1 arguments spread log-uniformly over 1e-8..1e8 with both
- * signs on the current device (default stream; the call waits) and stores in
- * *max_ulp the largest distance, in units in the last place, from the correctly
- * rounded IEEE quotient.  Errors: HGKS_EINVAL (n < 1, max_ulp NULL), HGKS_ECUDA. */
+/* Check of the flux's reciprocal and reciprocal square root (a measurement
+ * helper like the probe above; the paper has no counterpart).  The flux forms 1/x
+ * and 1/sqrt(x) as the hardware's approximations refined by two Newton-Raphson
+ * steps instead of a division or square root; this evaluates both on n >= 1
+ * arguments spread log-uniformly over 1e-8..1e8 (both signs for 1/x) on the
+ * current device (default stream; the call waits) and stores in max_ulp[0] the
+ * largest distance of 1/x, in units in the last place, from the correctly
+ * rounded IEEE quotient, in max_ulp[1] that of 1/sqrt(x) from IEEE division by
+ * the IEEE square root (itself up to one rounding away).  max_ulp: 2 entries.
+ * Errors: HGKS_EINVAL (n < 1, max_ulp NULL), HGKS_ECUDA. */
 int hgks_check_reciprocal(long long n, unsigned long long* max_ulp);
 
 /* ------------------------------------------------------------------------ */

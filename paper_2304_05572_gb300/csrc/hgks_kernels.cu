@@ -1162,10 +1162,11 @@ cudaError_t launch_dfma_probe(cudaStream_t st, int blocks, int iters)
 }
 
 // ---------------------------------------------------------------- reciprocal check
-// The flux's Newton-refined reciprocal (rcp_nr) against IEEE division on n arguments spread
-// log-uniformly over 1e-8..1e8 with both signs (splitmix64 hashes of the index); the largest
-// difference in units in the last place goes to g_rcp_max_ulp.
-__device__ unsigned long long g_rcp_max_ulp;
+// The flux's Newton-refined reciprocal (rcp_nr) against IEEE division, and its reciprocal square
+// root (rsqrt_nr) against IEEE division by the IEEE square root, on n arguments spread
+// log-uniformly over 1e-8..1e8 (both signs for the reciprocal; splitmix64 hashes of the index);
+// the largest differences in units in the last place go to g_rcp_max_ulp[0], [1].
+__device__ unsigned long long g_rcp_max_ulp[2];
 
 __global__ void k_rcp_check(long long n)
 {
@@ -1178,21 +1179,24 @@ __global__ void k_rcp_check(long long n)
     const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);      // [0, 1)
     double x = exp10(16.0 * u - 8.0);
     if (z & 1) x = -x;
-    const double a = rcp_nr(x), b = 1.0 / x;
-    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-    const unsigned long long d = (unsigned long long)(ia > ib ? ia - ib : ib - ia);
-    atomicMax(&g_rcp_max_ulp, d);
+    auto ulps = [](double a, double b) {
+        const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+        return (unsigned long long)(ia > ib ? ia - ib : ib - ia);
+    };
+    atomicMax(&g_rcp_max_ulp[0], ulps(rcp_nr(x), 1.0 / x));
+    const double ax = fabs(x);
+    atomicMax(&g_rcp_max_ulp[1], ulps(rsqrt_nr(ax), 1.0 / sqrt(ax)));
 }
 
 cudaError_t rcp_check(long long n, unsigned long long* max_ulp)
 {
-    const unsigned long long zero = 0;
-    cudaError_t e = cudaMemcpyToSymbol(g_rcp_max_ulp, &zero, sizeof(zero));
+    const unsigned long long zero[2] = {0, 0};
+    cudaError_t e = cudaMemcpyToSymbol(g_rcp_max_ulp, zero, sizeof(zero));
     if (e != cudaSuccess) return e;
     k_rcp_check<<<(unsigned)((n + 255) / 256), 256>>>(n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return cudaMemcpyFromSymbol(max_ulp, g_rcp_max_ulp, sizeof(*max_ulp));
+    return cudaMemcpyFromSymbol(max_ulp, g_rcp_max_ulp, 2 * sizeof(*max_ulp));
 }
 
 int debug_bounds_read(unsigned long long* count, unsigned long long* first)

@@ -498,7 +498,7 @@ struct Mom {
 // Primitive description of one Maxwellian (Eq. (3)): h = 1/(2 lambda) = p/rho.
 template <int DIM>
 struct MState {
-    double rho, ri, U, V, p, h, lam, E;
+    double rho, ri, U, V, p, h, lam, sl, E;
     double q, lam2c, two_lam;      // slope-solve constants: q = |U|^2 + Kq h, lam2c = lam^2 (4/Kq)/rho,
                                    // two_lam = 2 lam/rho (the 1/rho of <a> = dW/rho folded in)
 };
@@ -537,6 +537,24 @@ HGKS_HD __forceinline__ double rcp_nr(double x)
 #endif
 }
 
+// 1/sqrt(x), x > 0, likewise: the hardware's approximation refined by two Newton-Raphson steps
+// for 1/sqrt(x), y <- y + y (1 - x y^2) / 2 (each roughly squares the relative error).  The host
+// build divides by the square root.
+HGKS_HD __forceinline__ double rsqrt_nr(double x)
+{
+#ifdef __CUDA_ARCH__
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hx = 0.5 * x;
+    double t = fma(-hx * y, y, 0.5);
+    y = fma(y, t, y);
+    t = fma(-hx * y, y, 0.5);
+    return fma(y, t, y);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
 template <int DIM>
 HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MState<DIM>& s)
 {
@@ -548,7 +566,8 @@ HGKS_HD __forceinline__ bool make_state(const double* W, const FluxConst& fc, MS
     double mu2 = DIM == 2 ? fma(W[1], s.U, W[2] * s.V) : W[1] * s.U;
     s.p = fc.gm1 * fma(-0.5, mu2, s.E);
     s.h = s.p * s.ri;
-    s.lam = 0.5 * rcp_nr(s.h);
+    s.sl = rsqrt_nr(2.0 * s.h);                 // sqrt(lambda), lambda = 1/(2h)
+    s.lam = s.sl * s.sl;
     s.q = fma(s.U, s.U, fma(s.V, s.V, fc.Kq * s.h));
     s.two_lam = 2.0 * s.lam * s.ri;
     s.lam2c = s.lam * fc.cslope * (0.5 * s.two_lam);
@@ -831,7 +850,7 @@ HGKS_HD __forceinline__ double erfc_nonneg(double y, double ey)
 template <int DIM>
 HGKS_HD __forceinline__ void half_moments(const MState<DIM>& s, int sign, const FluxConst& fc, Mom<DIM>& m)
 {
-    const double sl = sqrt(s.lam);
+    const double sl = s.sl;
     const double x = sl * s.U;
     const double ex2 = exp(-x * x);
     const double e = ex2 * (0.56418958354775628695 * s.p * sl);   // rho h sqrt(lam)/sqrt(pi), rho h = p

@@ -363,14 +363,14 @@ def hgks_debug_bounds():
     return bool(rc), n.value, a.value
 
 
-def hgks_check_reciprocal(n: int = 1 << 24) -> int:
-    """Largest distance in ulps of the flux's Newton-refined reciprocal from IEEE division
-    over n arguments (see include/hgks.h)."""
-    u = ctypes.c_ulonglong(0)
-    rc = lib().hgks_check_reciprocal(int(n), ctypes.byref(u))
+def hgks_check_reciprocal(n: int = 1 << 24):
+    """(1/x, 1/sqrt(x)): largest distances in ulps of the flux's Newton-refined reciprocal and
+    reciprocal square root from their IEEE counterparts over n arguments (see include/hgks.h)."""
+    u = (ctypes.c_ulonglong * 2)()
+    rc = lib().hgks_check_reciprocal(int(n), u)
     if rc != HGKS_OK:
         raise HGKSError(rc, lib().hgks_last_error(None).decode())
-    return u.value
+    return u[0], u[1]
 
 
 def hgks_probe_fp64(stream=None):
