@@ -39,8 +39,46 @@ __device__ __forceinline__ ex xfma(ex a, ex b, ex c) { return ex(__fma_rn(a.v, b
 __device__ __forceinline__ ex xabs(ex a) { return ex(fabs(a.v)); }
 __device__ __forceinline__ ex xsqrt(ex a) { return ex(__dsqrt_rn(a.v)); }
 
-// Free-order FP64 with the same interface: the compiler may contract a*b + c into an FMA.  Used
-// where the outputs only feed the flux (the tangential WENO-AO pass), never a flag decision.
+// 1/x in free-order arithmetic (the flux, the tangential WENO-AO pass): the hardware's approximate reciprocal refined by two
+// Newton-Raphson steps for 1/x, r <- r + r (1 - x r), each of which squares the relative error;
+// within 1 ulp of the correctly rounded quotient for the normal x the flux meets (checked against
+// IEEE division by hgks_check_reciprocal).  A zero x gives a NaN, which the flux's physical-state
+// tests reject as they rejected the infinity of 1/0.  The host build divides.
+HGKS_HD __forceinline__ double rcp_nr(double x)
+{
+#ifdef __CUDA_ARCH__
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+#else
+    return 1.0 / x;
+#endif
+}
+
+// 1/sqrt(x), x > 0, likewise: the hardware's approximation refined by two Newton-Raphson steps
+// for 1/sqrt(x), y <- y + y (1 - x y^2) / 2 (each roughly squares the relative error).  The host
+// build divides by the square root.
+HGKS_HD __forceinline__ double rsqrt_nr(double x)
+{
+#ifdef __CUDA_ARCH__
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hx = 0.5 * x;
+    double t = fma(-hx * y, y, 0.5);
+    y = fma(y, t, y);
+    t = fma(-hx * y, y, 0.5);
+    return fma(y, t, y);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
+// Free-order FP64 with the same interface: the compiler may contract a*b + c into an FMA, and
+// divisions and square roots go through the Newton-refined reciprocals above.  Used where the
+// outputs only feed the flux (the tangential WENO-AO pass), never a flag decision.
 struct fx {
     double v;
     __device__ __forceinline__ fx() {}
@@ -49,11 +87,11 @@ struct fx {
 __device__ __forceinline__ fx operator+(fx a, fx b) { return fx(a.v + b.v); }
 __device__ __forceinline__ fx operator-(fx a, fx b) { return fx(a.v - b.v); }
 __device__ __forceinline__ fx operator*(fx a, fx b) { return fx(a.v * b.v); }
-__device__ __forceinline__ fx operator/(fx a, fx b) { return fx(a.v / b.v); }
+__device__ __forceinline__ fx operator/(fx a, fx b) { return fx(a.v * rcp_nr(b.v)); }
 __device__ __forceinline__ fx operator-(fx a) { return fx(-a.v); }
 __device__ __forceinline__ fx xfma(fx a, fx b, fx c) { return fx(fma(a.v, b.v, c.v)); }
 __device__ __forceinline__ fx xabs(fx a) { return fx(fabs(a.v)); }
-__device__ __forceinline__ fx xsqrt(fx a) { return fx(sqrt(a.v)); }
+__device__ __forceinline__ fx xsqrt(fx a) { return fx(a.v * rsqrt_nr(a.v)); }
 
 template <typename T> struct exact_order { static constexpr bool value = false; };
 template <> struct exact_order<ex> { static constexpr bool value = true; };
@@ -150,7 +188,7 @@ __device__ __forceinline__ void ao_weights(const T* q, const AOConst& k, T* wb)
         const double e0 = b[0].v + k.eps, e1 = b[1].v + k.eps, e2 = b[2].v + k.eps, e3 = b[3].v + k.eps;
         const double e01 = e0 * e1, e23 = e2 * e3, prod = e01 * e23;
         if (prod > 0.0 && prod < 1e300) {
-            const double di = d.v / prod;
+            const double di = d.v * rcp_nr(prod);
             r[0] = T(di * (e1 * e23)); r[1] = T(di * (e0 * e23));
             r[2] = T(di * (e3 * e01)); r[3] = T(di * (e2 * e01));
             done = true;
@@ -516,43 +554,6 @@ HGKS_HD __forceinline__ double dotv(const double* a, const double* b)
 #pragma unroll
     for (int k = 1; k < NV; k++) s = fma(a[k], b[k], s);
     return s;
-}
-
-// 1/x in the flux's free-order arithmetic: the hardware's approximate reciprocal refined by two
-// Newton-Raphson steps for 1/x, r <- r + r (1 - x r), each of which squares the relative error;
-// within 1 ulp of the correctly rounded quotient for the normal x the flux meets (checked against
-// IEEE division by hgks_check_reciprocal).  A zero x gives a NaN, which the flux's physical-state
-// tests reject as they rejected the infinity of 1/0.  The host build divides.
-HGKS_HD __forceinline__ double rcp_nr(double x)
-{
-#ifdef __CUDA_ARCH__
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
-#else
-    return 1.0 / x;
-#endif
-}
-
-// 1/sqrt(x), x > 0, likewise: the hardware's approximation refined by two Newton-Raphson steps
-// for 1/sqrt(x), y <- y + y (1 - x y^2) / 2 (each roughly squares the relative error).  The host
-// build divides by the square root.
-HGKS_HD __forceinline__ double rsqrt_nr(double x)
-{
-#ifdef __CUDA_ARCH__
-    double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double hx = 0.5 * x;
-    double t = fma(-hx * y, y, 0.5);
-    y = fma(y, t, y);
-    t = fma(-hx * y, y, 0.5);
-    return fma(y, t, y);
-#else
-    return 1.0 / sqrt(x);
-#endif
 }
 
 template <int DIM>
