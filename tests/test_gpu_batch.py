@@ -25,6 +25,9 @@ def _cases_2d():
     out.append((cfg, W))
     cfg, W, _ = P.viscous_shock_tube(40, 20, Re=300.0)
     out.append((cfg, W))
+    # Navier-Stokes with the Prandtl fix (its own flux variant)
+    cfg, W, _ = P.viscous_shock_tube(48, 24, Re=1000.0, prandtl=0.73)
+    out.append((cfg, W))
     # WENO-AO everywhere at 128x128: every compacted pass holds 34572 to 66048 items, above the
     # size from which the passes give each item one lane (the others here use lane groups)
     cfg, W, _ = P.random_smooth_2d(128, 128)
