@@ -81,9 +81,9 @@ NONFLUX_FLOP_PER_CELL_STAGE = {"linear": 2721.3, "wenoao": 19486.7, "hybrid": 35
                                "hybrid_troubled_fraction": 0.004106}
 # DRAM bytes (read + write) per flux launch (both sweeps), one ncu pass over a whole 1024^2 step
 # with the caches carried from kernel to kernel (--cache-control none), as the step runs: first
-# stage 274.6 MB read + 118.3 MB written, second stage 275.9 + 61.7 MB; per Gauss point of the
+# stage 275.5 MB read + 118.6 MB written, second stage 275.6 + 61.5 MB; per Gauss point of the
 # launch (4 * 1024 * 1025 of them).
-FLUX_DRAM_BYTES_PER_GP = (274.63e6 + 118.26e6 + 275.91e6 + 61.70e6) / 2 / (4 * 1024 * 1025)
+FLUX_DRAM_BYTES_PER_GP = (275.49e6 + 118.56e6 + 275.58e6 + 61.50e6) / 2 / (4 * 1024 * 1025)
 
 
 def algorithmic_flop_per_cell_stage(n, troubled_fraction):
