@@ -184,6 +184,15 @@ def test_wenoao_passes_in_both_lane_forms(nx, ny):
     check_step(cfg, Wo, "wenoao %dx%d, second step" % (nx, ny))
 
 
+def test_wenoao_1d_one_lane_form():
+    """WENO-AO everywhere on a 20000-cell Sod tube: 40002 troubled sides per pass, above the
+    switch to one item per lane (the 3-component form of the normal pass)."""
+    cfg, W, _ = P.sod_1d(20000)
+    cfg["recon_mode"] = "wenoao"
+    Wo, _, _, _ = check_step(cfg, W, "wenoao sod 20000")
+    check_step(cfg, Wo, "wenoao sod 20000, second step")
+
+
 def test_paper_riemann_configurations():
     for fn in (P.riemann_config1, P.riemann_config6):
         cfg, W, _ = fn(40)
